@@ -1,0 +1,317 @@
+"""All-pairs CCM benchmark: cross-map pairs per second on one GB300.
+
+A step is one pass of the whole hot path over the synthetic workload:
+phase 1 (optimal E of every series) + phase 2 (kNN tables, lookup and rho
+for every library x target pair), with the N x N rho written to device
+memory.  Default workload: N = 101,729 coupled logistic maps, T = 1,500.
+
+    python bench.py --gpus N --steps K --warmup W [--impl reference]
+
+Prints one JSON line on rank 0.  `value` is whole-job pairs/s from CUDA
+events on the launching stream (max over ranks); `roofline` is for the
+dominant kernel (lookup) from per-launch events taken live in the timed
+region; `e2e` is the same metric through the public API with host buffers
+(H2D of the series and D2H of rho inside the timed region);
+`cpu_baseline` is the FP64 oracle on a bounded sample on this host's cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (N, T, density, b_max, E_max)
+    "n101729_t1500": (101729, 1500, 0.0001, 0.02, 20),
+    "n16384_t1500": (16384, 1500, 0.01, 0.02, 20),
+    "n2048_t1500": (2048, 1500, 0.01, 0.02, 20),
+    "n64_t500": (64, 500, 0.05, 0.05, 10),
+}
+METRIC = "cross-map pairs/s at N=101,729,T=1500 (1 GB300) + % HBM roofline vs plain FP32"
+UNIT = "pairs/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _algorithmic_bytes_per_pair(N, T, s_y):
+    # rho write (4 B) + every target read once + every library read once
+    # + optE, spread over the N^2 pairs.
+    return 4.0 + (N * T * s_y + N * T * 4.0 + 4.0 * N) / float(N) / float(N)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(Y, optE, sample_rows, N, E_max=20):
+    """The FP64 oracle, as it stands, on `sample_rows` library rows x all
+    targets (phase 2) plus phase 1 of as many series; scaled to pairs/s.
+    optE=None: the targets' E are the oracle's phase-1 values of the sampled
+    series, repeated over all N targets."""
+    from oracle import oracle as orc
+
+    cores = orc.default_threads()
+    if sample_rows <= 0:
+        sample_rows = 2 * cores
+    rows = np.arange(sample_rows, dtype=np.int64)
+    t0 = time.perf_counter()
+    oE, _ = orc.optimal_E(Y[:sample_rows], E_max, nthreads=cores)
+    t1 = time.perf_counter()
+    if optE is None:
+        optE = np.resize(oE, N).astype(np.int32)
+    orc.ccm_rho_rows(Y, optE, rows=rows, nthreads=cores)
+    t2 = time.perf_counter()
+    # whole-path time for N^2 pairs, extrapolated: phase 1 for N series and
+    # phase 2 for N library rows.
+    per_series_p1 = (t1 - t0) / sample_rows
+    per_row_p2 = (t2 - t1) / sample_rows
+    est = N * (per_series_p1 + per_row_p2)
+    return {"value": float(N) * N / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"phase 1 on {sample_rows} series + phase 2 for {sample_rows} library rows x all {N} targets "
+                      f"({t2 - t0:.1f} s of CPU wall time), extrapolated to N={N}"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm (host cores; rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import edm_synth
+
+    N, T, dens, bmax, E_max = WORKLOADS[args.workload]
+    Y = edm_synth.coupled_logistic(N, T, dens, bmax, 0, 1)
+    # phase 1 of all N series is hours of FP64 CPU work: each step times the
+    # oracle on a bounded sample (see cpu_baseline) and scales to N^2 pairs.
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(Y, None, args.cpu_rows, N, E_max)
+    val = cb["value"]
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(N) * N / val * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "N": N, "T": T, "E_max": E_max},
+            "cpu_baseline": cb, "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n101729_t1500", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--cpu-rows", type=int, default=0, help="library rows the oracle times (0: 2 x cores)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import edm_synth
+    import paper_2011_11082_gb300 as edm
+    from paper_2011_11082_gb300 import _abi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    lib = _abi.load()
+
+    N, T, dens, bmax, E_max = WORKLOADS[args.workload]
+    # independent problems per rank (weak scaling): rank r uses data seed r
+    Y = edm_synth.coupled_logistic(N, T, dens, bmax, seed_data=rank, seed_noise=1 + rank)
+    Yd = torch.from_numpy(Y).to(dev)
+    prec = edm.EDM_PRECISION_FP16_TARGETS if args.precision == "fp16" else edm.EDM_PRECISION_FP32
+    rho = torch.empty((N, N), dtype=torch.float32, device=dev)
+    ws = torch.empty(edm.edm_ccm_workspace_bytes(N, T, precision=prec), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        optE, _ = edm.edm_optimal_E(Yd, E_max=E_max, return_rho=False)
+        edm.edm_ccm_rho(Yd, optE, precision=prec, out=rho, workspace=ws)
+        return optE
+
+    for _ in range(args.warmup):
+        optE = step()
+    torch.cuda.synchronize()
+
+    launches0 = [lib.edm_launch_count(k) for k in range(4)]
+    lib.edm_profile_enable(1)
+    for k in range(4):
+        lib.edm_profile_read(k, None, None, None)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        optE = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    lib.edm_profile_enable(0)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = sum(lib.edm_launch_count(k) - launches0[k] for k in range(4))
+    prof = {}
+    for k in range(4):
+        m, n, u = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        lib.edm_profile_read(k, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
+        prof[_abi.KERNEL_NAMES[k]] = {"ms": m.value / args.steps, "launches": n.value // args.steps,
+                                      "units": u.value / args.steps}
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * float(N) * N / (ms / 1e3)
+
+    # roofline of the dominant kernel (lookup): algorithmic bytes / time
+    peak, peak_kind = _peaks()
+    s_y = 2.0 if args.precision == "fp16" else 4.0
+    bpp = _algorithmic_bytes_per_pair(N, T, s_y)
+    lk = prof["lookup_kernel"]
+    lk_launches = max(1, lk["launches"])
+    per_launch_bytes = lk["units"] * bpp / lk_launches
+    per_launch_s = lk["ms"] / 1e3 / lk_launches
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": peak_kind, "kernel": "lookup_kernel",
+                "bytes_per_pair": bpp, "path_frac": (N * float(N) * bpp / (ms / 1e3) / 1e9) / peak}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        try:
+            Yh = torch.from_numpy(Y).pin_memory()
+            try:
+                rho_h = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
+                pinned = True
+            except Exception:
+                rho_h = torch.empty((N, N), dtype=torch.float32)
+                pinned = False
+            e2e_steps = max(1, min(args.steps, 2))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(e2e_steps):
+                Yd.copy_(Yh, non_blocking=True)
+                step()
+                rho_h.copy_(rho, non_blocking=pinned)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ems = e0.elapsed_time(e1) / e2e_steps
+            e2e = {"value": world * float(N) * N / (ems / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(Y.nbytes), "d2h_bytes_per_step": int(rho.numel() * 4),
+                   "host_buffers": "pinned" if pinned else "pageable"}
+            del rho_h
+        except Exception as ex:  # pragma: no cover
+            e2e = {"value": None, "unit": UNIT, "error": repr(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(Y, optE.cpu().numpy(), args.cpu_rows, N, E_max)
+
+    if rank == 0:
+        hist = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:].tolist()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16-targets/f32-accumulate",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "T": T, "E_max": E_max, "tau": 1, "Tp": 1,
+                       "precision": args.precision, "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)",
+                       "optE_histogram": hist},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "kernels": prof,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * edm.h -- C ABI of the GB300 (sm_103a) all-pairs Convergent Cross Mapping
+ * library (the data-parallel hot path of mpEDM, arXiv 2011.11082).
+ *
+ * The paper states the problem as: input N time series of length L, the
+ * maximum embedding dimension E_max and the lag tau; output the optimal
+ * embedding dimension of every series and the N x N causal map rho
+ * (Sec. III-A, Algorithm 1 and Algorithm 2).  The entry points below follow
+ * that statement.
+ *
+ * Conventions for every entry point
+ *   - Pointers named Y, x, optE, rho, idx, w, grad_* and ws are DEVICE
+ *     pointers owned by the caller; the library never frees them.  Pointers
+ *     to edm_params and to host arrays are read during the call only.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; unless stated otherwise a call does
+ *     not synchronise and returns before the GPU finishes.
+ *   - Series are float32, series-major: series i occupies Y[i*ldY .. i*ldY+T).
+ *   - Return value: EDM_OK (0) or an EDM_ERR_* code.  EDM_ERR_CUDA keeps the
+ *     CUDA error for edm_status_string() and edm_last_cuda_error().
+ *   - Non-finite input values are the caller's responsibility (results are
+ *     then undefined but every memory access stays in bounds).
+ *   - There is no CPU fallback: without a usable sm_103a device every
+ *     compute entry point returns EDM_ERR_CUDA.
+ */
+#ifndef EDM_H
+#define EDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EDM_OK 0
+#define EDM_ERR_INVALID 1     /* bad argument: null pointer, size, or T too short */
+#define EDM_ERR_CUDA 2        /* a CUDA call failed (see edm_last_cuda_error) */
+#define EDM_ERR_WORKSPACE 3   /* ws too small; see the matching *_workspace_bytes */
+#define EDM_ERR_TIMEOUT 4     /* a bounded device wait gave up */
+#define EDM_ERR_UNSUPPORTED 5 /* valid request outside this build's limits */
+
+/* Largest embedding dimension the kernels are built for. */
+#define EDM_MAX_E 20
+/* Longest series the kernels accept (indices are kept in 16 bits). */
+#define EDM_MAX_T 65535
+
+#define EDM_PRECISION_FP32 0         /* targets staged as float32 */
+#define EDM_PRECISION_FP16_TARGETS 1 /* targets staged as float16, FP32 accumulation */
+
+/* flags */
+#define EDM_FLAG_NONE 0u
+
+typedef struct edm_params {
+    int32_t E_max;            /* phase 1 searches E = 1..E_max (<= EDM_MAX_E) */
+    int32_t tau;              /* lag between embedding coordinates, >= 1 */
+    int32_t Tp;               /* prediction horizon, >= 0 (1 = one step ahead) */
+    int32_t exclusion_radius; /* phase 2: a query skips candidates with |s-t| <= r;
+                                 0 = itself only, -1 = keep itself */
+    int32_t precision;        /* EDM_PRECISION_* (phase 2 target staging) */
+    uint32_t flags;           /* EDM_FLAG_* */
+} edm_params;
+
+/*
+ * Phase 1, simplex projection (Algorithm 1 lines 1-11; Sec. II-B).
+ * For every series i: library = first floor(T/2) samples, target = the rest,
+ * both embedded within themselves with lags (0, tau, .., (E-1)tau) counted
+ * backwards; each target point's E+1 nearest library points (ascending
+ * distance, ties to the smaller index) give the forecast
+ * sum_n w_n lib(s_n+Tp), w = exp(-d/d_1)/sum; rho_E = Pearson(observed,
+ * forecast); optE[i] = argmax_E rho_E (NaN never wins, ties -> smaller E,
+ * all-NaN -> 1).
+ *   Y         [N][ldY] float32, ldY >= T
+ *   optE      [N] int32 out
+ *   rho_by_E  [N][E_max] float32 out, or NULL
+ * Requires floor(T/2) - Tp - (E_max-1)*tau >= E_max + 1 and
+ * T - floor(T/2) - Tp - (E_max-1)*tau >= 2, else EDM_ERR_INVALID.
+ */
+int edm_optimal_E(const float *Y, int64_t N, int64_t T, int64_t ldY, const edm_params *params,
+                  int32_t *optE, float *rho_by_E, void *stream);
+
+/*
+ * Phase 2 kNN tables (Algorithm 2 lines 4-6, Algorithms 3/4; the table
+ * reuse of Sec. III-B).  For each of n_lib library series and one E: every
+ * embedded point t in [(E-1)tau, T-1-Tp] (row r = t-(E-1)tau) gets its E+1
+ * nearest embedded points s of the same series in the same range
+ * (skipping |s-t| <= exclusion_radius), ascending (d^2, s), and the
+ * normalised weights exp(-d/d_1)/sum.  Neighbour order is exact with
+ * respect to float64 distances of the float32 inputs.
+ *   Y     [n_lib][ldY] float32
+ *   idx   [n_lib][Tq][E+1] int32 out: neighbour times s (not shifted by Tp)
+ *   w     [n_lib][Tq][E+1] float32 out
+ *   Tq    must equal T - Tp - (E-1)*tau
+ */
+int edm_knn_table(const float *Y, int64_t n_lib, int64_t T, int64_t ldY, int32_t E,
+                  const edm_params *params, int32_t *idx, float *w, int64_t Tq, void *stream);
+
+/*
+ * Phase 2 cross map (Algorithm 2 lines 8-11; Algorithm 5 lookup; corrcoef).
+ * For libraries i in [lib_begin, lib_begin+lib_count) and every target j:
+ * prediction p(t) = sum_n w[t,n] y_j(s_n+Tp) with library i's table at
+ * E = optE[j], observation o(t) = y_j(t+Tp), rho(i,j) = Pearson(o, p).
+ *   Y      [N][ldY] float32
+ *   optE   [N] int32 (device), each in 1..EDM_MAX_E
+ *   rho    TARGET-MAJOR output: rho[j*ld_rho + (i - lib_begin)] = rho(i, j)
+ *          for every target j in 0..N-1; ld_rho >= lib_count.  (The
+ *          library-major causal map of the paper is the transpose view.)
+ *   ws     device workspace of at least edm_ccm_workspace_bytes(N, T, params)
+ * This call synchronises `stream` once, to read optE on the host and plan
+ * the target grouping; everything else is enqueued asynchronously.
+ */
+int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                int64_t lib_begin, int64_t lib_count, const edm_params *params,
+                float *rho, int64_t ld_rho, void *ws, size_t ws_bytes, void *stream);
+
+/* Workspace edm_ccm_rho needs for N series of length T (bytes). */
+size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
+
+/* Human-readable text for a status code (includes the CUDA error if any). */
+const char *edm_status_string(int status);
+
+/* The CUDA error behind the last EDM_ERR_CUDA on this thread (0 if none). */
+int edm_last_cuda_error(void);
+
+/* Library version, e.g. 0x000100 = 0.1.0. */
+int edm_version(void);
+
+/*
+ * Launch accounting and kernel timing (instrumentation, not part of the
+ * method).  Kernel ids: */
+#define EDM_KERNEL_SIMPLEX 0 /* phase 1 simplex projection */
+#define EDM_KERNEL_KNN 1     /* phase 2 kNN tables */
+#define EDM_KERNEL_PREP 2    /* target staging */
+#define EDM_KERNEL_LOOKUP 3  /* fused lookup + rho */
+#define EDM_KERNEL_COUNT 4
+/*
+ * edm_launch_count: launches of that kernel since load (always counted).
+ * edm_profile_enable(1): from now on record a CUDA event pair on the
+ *   launching stream around every launch (process-wide, not thread-safe).
+ * edm_profile_read: synchronise the recorded events and return, per kernel,
+ *   the summed device time (ms), the launches timed and the work units
+ *   they processed (pairs for LOOKUP, series for SIMPLEX, library tables
+ *   for KNN, targets for PREP); then forget them.
+ */
+int64_t edm_launch_count(int kernel);
+int edm_profile_enable(int on);
+int edm_profile_read(int kernel, double *ms, int64_t *launches, double *units);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDM_H */

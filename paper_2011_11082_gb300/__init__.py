@@ -1,0 +1,128 @@
+"""GB300-native all-pairs Convergent Cross Mapping (the mpEDM hot path).
+
+Thin Python binding over the C ABI of ``include/edm.h`` (libedm.so, built
+in-tree for sm_103a).  Functions carry the C names; they only marshal torch
+CUDA tensors into pointers, sizes and the current stream.  Every step of the
+computation runs in the CUDA kernels; there is no CPU fallback, and the
+first call fails loudly if the library or a GPU is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi
+from ._abi import (
+    EDM_MAX_E,
+    EDM_PRECISION_FP16_TARGETS,
+    EDM_PRECISION_FP32,
+    EdmError,
+    edm_params,
+)
+
+__all__ = [
+    "edm_optimal_E",
+    "edm_knn_table",
+    "edm_ccm_rho",
+    "edm_ccm_workspace_bytes",
+    "ccm",
+    "make_params",
+    "EdmError",
+    "EDM_MAX_E",
+]
+
+
+def make_params(E_max=20, tau=1, Tp=1, exclusion_radius=0, precision=EDM_PRECISION_FP32, flags=0) -> edm_params:
+    return edm_params(int(E_max), int(tau), int(Tp), int(exclusion_radius), int(precision), int(flags))
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_f32(Y: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dtype == torch.float32):
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if Y.dim() != 2 or Y.stride(1) != 1:
+        raise TypeError(f"{name} must be 2-D [N][T] with unit stride along T")
+    return Y
+
+
+def edm_optimal_E(Y: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, return_rho: bool = True,
+                  stream=None):
+    """Phase 1 (simplex projection): optE int32[N] and rho_by_E float32[N][E_max]."""
+    lib = _abi.load()
+    Y = _dev_f32(Y, "Y")
+    N, T = Y.shape
+    optE = torch.empty(N, dtype=torch.int32, device=Y.device)
+    rho = torch.empty((N, E_max), dtype=torch.float32, device=Y.device) if return_rho else None
+    p = make_params(E_max=E_max, tau=tau, Tp=Tp)
+    st = lib.edm_optimal_E(Y.data_ptr(), N, T, Y.stride(0), ctypes.byref(p), optE.data_ptr(),
+                           rho.data_ptr() if rho is not None else None, _stream(stream))
+    _abi.check(st, "edm_optimal_E")
+    return optE, rho
+
+
+def edm_knn_table(Y: torch.Tensor, E: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0, stream=None):
+    """Phase-2 kNN tables of every row of Y at dimension E:
+    idx int32[n][Tq][E+1] (neighbour times, unshifted) and w float32[n][Tq][E+1]."""
+    lib = _abi.load()
+    Y = _dev_f32(Y, "Y")
+    n, T = Y.shape
+    Tq = T - Tp - (E - 1) * tau
+    if Tq < 1:
+        raise ValueError("series too short for this E")
+    idx = torch.empty((n, Tq, E + 1), dtype=torch.int32, device=Y.device)
+    w = torch.empty((n, Tq, E + 1), dtype=torch.float32, device=Y.device)
+    p = make_params(E_max=E, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius)
+    st = lib.edm_knn_table(Y.data_ptr(), n, T, Y.stride(0), E, ctypes.byref(p), idx.data_ptr(), w.data_ptr(), Tq,
+                           _stream(stream))
+    _abi.check(st, "edm_knn_table")
+    return idx, w
+
+
+def edm_ccm_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,
+                            precision: int = EDM_PRECISION_FP32) -> int:
+    lib = _abi.load()
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    return int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
+
+
+def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_count: int | None = None,
+                tau: int = 1, Tp: int = 1, exclusion_radius: int = 0, precision: int = EDM_PRECISION_FP32,
+                out: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Phase 2 cross map for libraries [lib_begin, lib_begin+lib_count).
+
+    Returns the TARGET-MAJOR block ``out[j][i - lib_begin] = rho(library i ->
+    target j)`` of shape [N][lib_count]; ``out.t()`` is the library-major map."""
+    lib = _abi.load()
+    Y = _dev_f32(Y, "Y")
+    N, T = Y.shape
+    if lib_count is None:
+        lib_count = N - lib_begin
+    if not (optE.is_cuda and optE.dtype == torch.int32 and optE.numel() == N and optE.is_contiguous()):
+        raise TypeError("optE must be a contiguous int32 CUDA tensor of N entries")
+    if out is None:
+        out = torch.empty((N, lib_count), dtype=torch.float32, device=Y.device)
+    if not (out.is_cuda and out.dtype == torch.float32 and out.dim() == 2 and out.stride(1) == 1
+            and out.shape[0] == N and out.shape[1] >= lib_count):
+        raise TypeError("out must be a float32 CUDA tensor [N][>=lib_count] with unit inner stride")
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    need = int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)
+    st = lib.edm_ccm_rho(Y.data_ptr(), N, T, Y.stride(0), optE.data_ptr(), lib_begin, lib_count, ctypes.byref(p),
+                         out.data_ptr(), out.stride(0), workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _abi.check(st, "edm_ccm_rho")
+    return out
+
+
+def ccm(Y: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,
+        precision: int = EDM_PRECISION_FP32):
+    """Both phases: (optE, rho) with rho the library-major N x N view."""
+    optE, _ = edm_optimal_E(Y, E_max=E_max, tau=tau, Tp=Tp, return_rho=False)
+    rho_t = edm_ccm_rho(Y, optE, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    return optE, rho_t.t()

@@ -1,0 +1,380 @@
+// edm_api.cu -- the C ABI (include/edm.h): argument checks, the host-side
+// plan of the cross-map phase, and the kernel orchestration.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "launchers.h"
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+thread_local char g_msg[256];
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return EDM_ERR_CUDA;
+}
+
+#define EDM_CUDA(call)                                                                                                 \
+    do {                                                                                                               \
+        cudaError_t e_ = (call);                                                                                       \
+        if (e_ != cudaSuccess)                                                                                         \
+            return cuda_fail(e_);                                                                                      \
+    } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// --- launch accounting and optional per-launch event timing ----------------
+struct ProfRec {
+    cudaEvent_t a, b;
+    int kernel;
+    double units;
+};
+int64_t g_launches[EDM_KERNEL_COUNT] = {0, 0, 0, 0};
+bool g_prof = false;
+std::vector<ProfRec> g_recs;
+double g_ms[EDM_KERNEL_COUNT], g_units[EDM_KERNEL_COUNT];
+int64_t g_timed[EDM_KERNEL_COUNT];
+
+struct LaunchScope {
+    ProfRec rec{};
+    bool on;
+    cudaStream_t st;
+    LaunchScope(int kernel, cudaStream_t s, double units) : on(g_prof), st(s)
+    {
+        g_launches[kernel]++;
+        if (on) {
+            rec.kernel = kernel;
+            rec.units = units;
+            cudaEventCreate(&rec.a);
+            cudaEventCreate(&rec.b);
+            cudaEventRecord(rec.a, st);
+        }
+    }
+    ~LaunchScope()
+    {
+        if (on) {
+            cudaEventRecord(rec.b, st);
+            g_recs.push_back(rec);
+        }
+    }
+};
+
+int check_common(const edm_params *p)
+{
+    if (!p)
+        return EDM_ERR_INVALID;
+    if (p->tau < 1 || p->Tp < 0 || p->exclusion_radius < -1)
+        return EDM_ERR_INVALID;
+    if (p->precision != EDM_PRECISION_FP32 && p->precision != EDM_PRECISION_FP16_TARGETS)
+        return EDM_ERR_INVALID;
+    return EDM_OK;
+}
+
+// Candidates a phase-2 query is guaranteed to have at dimension E.
+int64_t ccm_min_candidates(int64_t T, int E, const edm_params *p)
+{
+    int64_t n = T - p->Tp - (int64_t)(E - 1) * p->tau;
+    if (p->exclusion_radius >= 0)
+        n -= 2 * (int64_t)p->exclusion_radius + 1;
+    return n;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 148;
+    return n > 0 ? n : 148;
+}
+
+// Budgets for the L2-resident working set of the cross-map phase.
+constexpr size_t kTileBlockBytes = 64ull << 20;  // target tiles per block
+constexpr size_t kTableBytes = 48ull << 20;      // kNN tables per library block
+
+int tq_pad(int64_t T, const edm_params *p) { return (int)(((T - p->Tp) + 31) / 32 * 32); }
+
+edm::TableLayout make_layout(uint32_t sel, int64_t T, const edm_params *p)
+{
+    edm::TableLayout lay;
+    lay.Tq_pad = tq_pad(T, p);
+    int64_t off = 0;
+    for (int E = 0; E <= EDM_MAX_E; ++E) {
+        lay.off_w[E] = -1;
+        lay.off_i[E] = -1;
+    }
+    for (int E = 1; E <= EDM_MAX_E; ++E) {
+        if (!((sel >> (E - 1)) & 1u))
+            continue;
+        lay.off_w[E] = off;
+        off += (int64_t)align256((size_t)(E + 1) * lay.Tq_pad * sizeof(float));
+        lay.off_i[E] = off;
+        off += (int64_t)align256((size_t)(E + 1) * lay.Tq_pad * sizeof(uint16_t));
+    }
+    lay.lib_stride = off;
+    return lay;
+}
+
+struct CcmWs {
+    size_t pi, omom, meta, tiles, tables, total;
+    int64_t n_tiles_max;
+    size_t table_bytes;
+};
+
+CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
+{
+    CcmWs w;
+    w.n_tiles_max = (N + 31) / 32 + EDM_MAX_E;
+    size_t off = 0;
+    w.pi = off;
+    off += align256((size_t)N * sizeof(int32_t));
+    w.omom = off;
+    off += align256((size_t)w.n_tiles_max * 32 * sizeof(float2));
+    w.meta = off;
+    off += align256((size_t)w.n_tiles_max * sizeof(edm::TileMeta));
+    w.tiles = off;
+    off += align256((size_t)w.n_tiles_max * (size_t)T * 32 * sizeof(float));
+    w.tables = off;
+    edm::TableLayout all = make_layout((1u << EDM_MAX_E) - 1u, T, p);
+    w.table_bytes = std::max(kTableBytes, (size_t)all.lib_stride);
+    off += align256(w.table_bytes);
+    w.total = off;
+    return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+int edm_version(void) { return 0x000100; }
+
+int64_t edm_launch_count(int kernel)
+{
+    return (kernel >= 0 && kernel < EDM_KERNEL_COUNT) ? g_launches[kernel] : -1;
+}
+
+int edm_profile_enable(int on)
+{
+    g_prof = on != 0;
+    return EDM_OK;
+}
+
+int edm_profile_read(int kernel, double *ms, int64_t *launches, double *units)
+{
+    if (kernel < 0 || kernel >= EDM_KERNEL_COUNT)
+        return EDM_ERR_INVALID;
+    for (ProfRec &r : g_recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        float f = 0.f;
+        cudaEventElapsedTime(&f, r.a, r.b);
+        g_ms[r.kernel] += f;
+        g_units[r.kernel] += r.units;
+        g_timed[r.kernel]++;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_recs.clear();
+    if (ms)
+        *ms = g_ms[kernel];
+    if (launches)
+        *launches = g_timed[kernel];
+    if (units)
+        *units = g_units[kernel];
+    g_ms[kernel] = 0.0;
+    g_units[kernel] = 0.0;
+    g_timed[kernel] = 0;
+    return EDM_OK;
+}
+
+int edm_last_cuda_error(void) { return g_last_cuda; }
+
+const char *edm_status_string(int status)
+{
+    switch (status) {
+    case EDM_OK: return "EDM_OK";
+    case EDM_ERR_INVALID: return "EDM_ERR_INVALID: invalid argument";
+    case EDM_ERR_WORKSPACE: return "EDM_ERR_WORKSPACE: workspace too small";
+    case EDM_ERR_TIMEOUT: return "EDM_ERR_TIMEOUT: a bounded device wait gave up";
+    case EDM_ERR_UNSUPPORTED: return "EDM_ERR_UNSUPPORTED: outside this build's limits";
+    case EDM_ERR_CUDA:
+        snprintf(g_msg, sizeof g_msg, "EDM_ERR_CUDA: %s", cudaGetErrorString((cudaError_t)g_last_cuda));
+        return g_msg;
+    default: return "unknown status";
+    }
+}
+
+int edm_optimal_E(const float *Y, int64_t N, int64_t T, int64_t ldY, const edm_params *params, int32_t *optE,
+                  float *rho_by_E, void *stream)
+{
+    int rc = check_common(params);
+    if (rc)
+        return rc;
+    if (!Y || !optE || N < 1 || T < 4 || ldY < T || params->E_max < 1)
+        return EDM_ERR_INVALID;
+    if (params->E_max > EDM_MAX_E || T > EDM_MAX_T)
+        return EDM_ERR_UNSUPPORTED;
+    const int64_t h = T / 2;
+    const int64_t span = (int64_t)(params->E_max - 1) * params->tau;
+    if (h - params->Tp - span < params->E_max + 1 || (T - h) - params->Tp - span < 2)
+        return EDM_ERR_INVALID;
+    if (T > edm::knn_max_T())
+        return EDM_ERR_UNSUPPORTED;
+    {
+        LaunchScope ls(EDM_KERNEL_SIMPLEX, (cudaStream_t)stream, (double)N);
+        EDM_CUDA(edm::launch_simplex(Y, N, (int)T, ldY, params->E_max, params->tau, params->Tp, optE, rho_by_E,
+                                     (cudaStream_t)stream));
+    }
+    return EDM_OK;
+}
+
+int edm_knn_table(const float *Y, int64_t n_lib, int64_t T, int64_t ldY, int32_t E, const edm_params *params,
+                  int32_t *idx, float *w, int64_t Tq, void *stream)
+{
+    int rc = check_common(params);
+    if (rc)
+        return rc;
+    if (!Y || !idx || !w || n_lib < 1 || T < 2 || ldY < T || E < 1)
+        return EDM_ERR_INVALID;
+    if (E > EDM_MAX_E || T > EDM_MAX_T || n_lib > 65535)
+        return EDM_ERR_UNSUPPORTED;
+    if (Tq != T - params->Tp - (int64_t)(E - 1) * params->tau || Tq < 1)
+        return EDM_ERR_INVALID;
+    if (ccm_min_candidates(T, E, params) < E + 1)
+        return EDM_ERR_INVALID;
+    if (T > edm::knn_max_T())
+        return EDM_ERR_UNSUPPORTED;
+    {
+        LaunchScope ls(EDM_KERNEL_KNN, (cudaStream_t)stream, (double)n_lib);
+        EDM_CUDA(edm::launch_knn_public(Y, ldY, (int)n_lib, (int)T, E, params->tau, params->Tp,
+                                        params->exclusion_radius, idx, w, (cudaStream_t)stream));
+    }
+    return EDM_OK;
+}
+
+size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params)
+{
+    if (!params || N < 1 || T < 2)
+        return 0;
+    return ccm_ws_layout(N, T, params).total;
+}
+
+int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE, int64_t lib_begin,
+                int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, void *ws, size_t ws_bytes,
+                void *stream)
+{
+    int rc = check_common(params);
+    if (rc)
+        return rc;
+    if (!Y || !optE || !rho || !ws || N < 1 || T < 2 || ldY < T)
+        return EDM_ERR_INVALID;
+    if (lib_begin < 0 || lib_count < 0 || lib_begin + lib_count > N || ld_rho < lib_count)
+        return EDM_ERR_INVALID;
+    if (T > EDM_MAX_T || N > 0x7fffffffLL)
+        return EDM_ERR_UNSUPPORTED;
+    if (params->precision != EDM_PRECISION_FP32)
+        return EDM_ERR_UNSUPPORTED;
+    if (T > edm::knn_max_T() || edm::lookup_smem_bytes((int)T) > 227u * 1024u)
+        return EDM_ERR_UNSUPPORTED;
+    const CcmWs L = ccm_ws_layout(N, T, params);
+    if (ws_bytes < L.total)
+        return EDM_ERR_WORKSPACE;
+    if (lib_count == 0)
+        return EDM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // --- plan: group the targets by their E (stable), tiles of 32 -------------
+    std::vector<int32_t> E_host((size_t)N);
+    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaStreamSynchronize(st));
+    int64_t count[EDM_MAX_E + 2] = {0};
+    for (int64_t j = 0; j < N; ++j) {
+        int E = E_host[(size_t)j];
+        if (E < 1 || E > EDM_MAX_E || ccm_min_candidates(T, E, params) < E + 1)
+            return EDM_ERR_INVALID;
+        count[E]++;
+    }
+    int64_t start[EDM_MAX_E + 2] = {0};
+    for (int E = 1; E <= EDM_MAX_E; ++E)
+        start[E + 1] = start[E] + count[E];
+    std::vector<int32_t> pi((size_t)N);
+    {
+        int64_t fill[EDM_MAX_E + 2];
+        memcpy(fill, start, sizeof fill);
+        for (int64_t j = 0; j < N; ++j)
+            pi[(size_t)fill[E_host[(size_t)j]]++] = (int32_t)j;
+    }
+    std::vector<edm::TileMeta> tiles;
+    for (int E = 1; E <= EDM_MAX_E; ++E)
+        for (int64_t c = 0; c < count[E]; c += 32)
+            tiles.push_back(edm::TileMeta{E, (int)(start[E] + c), (int)std::min<int64_t>(32, count[E] - c), 0});
+    const int n_tiles = (int)tiles.size();
+
+    unsigned char *wsb = (unsigned char *)ws;
+    int32_t *pi_d = (int32_t *)(wsb + L.pi);
+    float2 *omom_d = (float2 *)(wsb + L.omom);
+    edm::TileMeta *meta_d = (edm::TileMeta *)(wsb + L.meta);
+    float *tiles_d = (float *)(wsb + L.tiles);
+    uint8_t *tables_d = (uint8_t *)(wsb + L.tables);
+    EDM_CUDA(cudaMemcpyAsync(pi_d, pi.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    EDM_CUDA(cudaMemcpyAsync(meta_d, tiles.data(), tiles.size() * sizeof(edm::TileMeta), cudaMemcpyHostToDevice, st));
+    {
+        LaunchScope ls(EDM_KERNEL_PREP, st, (double)N);
+        EDM_CUDA(edm::launch_prep_targets(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles, tiles_d,
+                                          omom_d, st));
+    }
+
+    // --- target blocks (L2-sized) x library blocks ------------------------------
+    const size_t tile_bytes = (size_t)T * 32 * sizeof(float);
+    const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
+    const int sms = sm_count();
+    for (int tb0 = 0; tb0 < n_tiles; tb0 += tiles_per_block) {
+        const int ntb = std::min(tiles_per_block, n_tiles - tb0);
+        uint32_t sel = 0;
+        for (int t = tb0; t < tb0 + ntb; ++t)
+            sel |= 1u << (tiles[(size_t)t].E - 1);
+        const edm::TableLayout lay = make_layout(sel, T, params);
+        const int64_t per_block = std::min<int64_t>(65535, std::max<int64_t>(1, (int64_t)(L.table_bytes / (size_t)lay.lib_stride)));
+        for (int64_t lb0 = 0; lb0 < lib_count; lb0 += per_block) {
+            const int nlb = (int)std::min<int64_t>(per_block, lib_count - lb0);
+            {
+                LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel));
+                EDM_CUDA(edm::launch_knn_tables(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
+                                                params->exclusion_radius, sel, lay, tables_d, st));
+            }
+            edm::LookupArgs a;
+            a.tiles = tiles_d;
+            a.meta = meta_d;
+            a.pi = pi_d;
+            a.omom = omom_d;
+            a.tables = tables_d;
+            a.lay = lay;
+            a.T = (int)T;
+            a.tau = params->tau;
+            a.Tp = params->Tp;
+            a.tile_begin = tb0;
+            a.n_tiles = ntb;
+            a.n_lib = nlb;
+            int parts = (4 * sms + ntb - 1) / ntb;
+            parts = std::max(1, std::min(parts, (nlb + 7) / 8));
+            a.lib_parts = parts;
+            a.rho_col0 = lb0;
+            a.rho = rho;
+            a.ld_rho = ld_rho;
+            {
+                int64_t targets = 0;
+                for (int t = tb0; t < tb0 + ntb; ++t)
+                    targets += tiles[(size_t)t].count;
+                LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
+                EDM_CUDA(edm::launch_lookup(a, st));
+            }
+        }
+    }
+    return EDM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// edm_internal.cuh -- shared device helpers of the sm_103a CCM kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "edm.h"
+
+namespace edm {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+// Neighbour lists keep E+1 entries plus this many guard entries, so an
+// uncertain order at the k-th place can be settled in FP64 without a rescan.
+constexpr int kGuard = 2;
+constexpr int kKmax = EDM_MAX_E + 1 + kGuard;
+// Per-warp compaction buffer (candidates at or below the running threshold).
+constexpr int kCandCap = 64;
+// FP32 squared distances below this go through FP64 (near-duplicate points).
+constexpr float kNearDup = 1e-30f;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Ascending bitonic sort of one value per lane across the warp.
+__device__ __forceinline__ float warp_sort_asc(float v)
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            float o = __shfl_xor_sync(kFull, v, stride);
+            bool up = (lane & size) == 0;
+            bool lower = (lane & stride) == 0;
+            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return v;
+}
+
+// Lexicographic key of a (non-negative float distance, candidate index)
+// pair: the bit pattern of a non-negative float orders like the value.
+__device__ __forceinline__ unsigned long long dkey(float d, int s)
+{
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)s;
+}
+
+// Bound on |fl32(d2) - d2| for a sum of E squared differences accumulated
+// with fused multiply-adds from float inputs: (E+2) units of 2^-24 relative
+// (one rounding per difference, its square is exact in the FMA, one rounding
+// per accumulation), widened to E+3 for margin.
+__device__ __forceinline__ float d2_err(float d, int E) { return d * (float)(E + 3) * 5.9604645e-8f; }
+
+}  // namespace edm

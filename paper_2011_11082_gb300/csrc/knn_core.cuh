@@ -1,0 +1,378 @@
+// knn_core.cuh -- warp-cooperative exact kNN over all embedding dimensions.
+//
+// One warp serves one query point t.  Lane l owns the candidate slots
+// s = s_first + c0 + l + 32 j (j < J) of the current chunk and keeps their
+// squared distances in registers.  The distance grows by one lag per E
+// (d2_E = d2_{E-1} + (x_q(t-(E-1)tau) - x_c(s-(E-1)tau))^2), so one sweep
+// over the candidates serves every E in 1..E_lim; a bit mask selects the E
+// whose neighbour lists are wanted (Sec. III-B: one table per E, Algorithm 2).
+//
+// Selection per (query, E): the K-th smallest of the 32 lane minima is an
+// upper bound on the K-th smallest distance (K = E+1+kGuard), so only the
+// few candidates at or below it are compacted into a shared buffer, ranked
+// by (d2, s) and kept as a sorted list that carries over to the next chunk.
+//
+// Exactness (neighbours identical to the FP64 reference): the FP32 sum has a
+// known error bound (d2_err).  When every gap among the first E+2 entries
+// exceeds the bounds, the FP32 order is the FP64 order.  Otherwise the kept
+// entries are re-ranked with FP64 distances computed in the reference's
+// operation order; if even the guard entries cannot separate the k-th place
+// from the rest, the query falls back to an exhaustive FP64 selection.
+#pragma once
+
+#include "edm_internal.cuh"
+
+namespace edm {
+
+__host__ __device__ constexpr int list_off(int E) { return (E - 1) * E / 2 + (E - 1) * (1 + kGuard); }
+constexpr int kListTotal = list_off(EDM_MAX_E + 1);
+
+struct KnnWarpScratch {
+    float cd[kCandCap];
+    int cs[kCandCap];
+    float ld[kListTotal];
+    int ls[kListTotal];
+    double l64[kKmax];
+    int ls64[kKmax];
+    int lcount[EDM_MAX_E + 1];
+    int ovf[EDM_MAX_E + 1];
+    int cnt;
+    int pad;
+};
+
+struct KnnQuery {
+    const float *xq;  // query series (shared memory)
+    const float *xc;  // candidate series (shared memory)
+    int t;            // query time in xq
+    int s_first;      // first candidate time (slot 0)
+    int s_last;       // last candidate time
+    int tau;
+    int same;         // xq and xc are the same series (apply the exclusion radius)
+    int excl;
+    int E_lim;        // distances are grown for E = 1..E_lim
+    uint32_t sel;     // bit E-1: produce the neighbour list for E
+};
+
+// FP64 squared distance in the reference's operation order.
+__device__ __forceinline__ double dist64(const float *xq, int t, const float *xc, int s, int E, int tau)
+{
+    double d = 0.0;
+    for (int m = 0; m < E; ++m) {
+        double diff = __dsub_rn((double)xq[t - m * tau], (double)xc[s - m * tau]);
+        d = __dadd_rn(d, __dmul_rn(diff, diff));
+    }
+    return d;
+}
+
+__device__ __forceinline__ bool cand_ok(const KnnQuery &q, int s, int E)
+{
+    if (s < q.s_first || s > q.s_last || s < (E - 1) * q.tau)
+        return false;
+    if (q.same && q.excl >= 0 && abs(s - q.t) <= q.excl)
+        return false;
+    return true;
+}
+
+// Rank-select: the buffer holds c (<= kCandCap) entries; write the K
+// smallest by (d, s) in order into the list for E.  Returns the count kept.
+__device__ __forceinline__ int buffer_to_list(KnnWarpScratch &sc, int c, int K, int lo)
+{
+    const int lane = lane_id();
+    unsigned long long k0 = ~0ull, k1 = ~0ull;
+    float d0 = 0.f, d1 = 0.f;
+    int s0 = 0, s1 = 0;
+    if (lane < c) {
+        d0 = sc.cd[lane];
+        s0 = sc.cs[lane];
+        k0 = dkey(d0, s0);
+    }
+    if (lane + 32 < c) {
+        d1 = sc.cd[lane + 32];
+        s1 = sc.cs[lane + 32];
+        k1 = dkey(d1, s1);
+    }
+    int r0 = 0, r1 = 0;
+    for (int f = 0; f < c; ++f) {
+        unsigned long long kf = dkey(sc.cd[f], sc.cs[f]);
+        r0 += kf < k0;
+        r1 += kf < k1;
+    }
+    __syncwarp();
+    if (lane < c && r0 < K) {
+        sc.ld[lo + r0] = d0;
+        sc.ls[lo + r0] = s0;
+    }
+    if (lane + 32 < c && r1 < K) {
+        sc.ld[lo + r1] = d1;
+        sc.ls[lo + r1] = s1;
+    }
+    __syncwarp();
+    return c < K ? c : K;
+}
+
+// K-th smallest key among the first c buffered entries (c > K).
+__device__ __forceinline__ unsigned long long buffer_kth_key(KnnWarpScratch &sc, int c, int K)
+{
+    const int lane = lane_id();
+    unsigned long long k0 = lane < c ? dkey(sc.cd[lane], sc.cs[lane]) : ~0ull;
+    unsigned long long k1 = lane + 32 < c ? dkey(sc.cd[lane + 32], sc.cs[lane + 32]) : ~0ull;
+    int r0 = 0, r1 = 0;
+    for (int f = 0; f < c; ++f) {
+        unsigned long long kf = dkey(sc.cd[f], sc.cs[f]);
+        r0 += kf < k0;
+        r1 += kf < k1;
+    }
+    unsigned long long mine = ~0ull;
+    if (lane < c && r0 == K - 1)
+        mine = k0;
+    if (lane + 32 < c && r1 == K - 1)
+        mine = k1;
+    // exactly one lane holds it (keys are distinct); min-reduce
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(kFull, mine, o);
+        mine = other < mine ? other : mine;
+    }
+    return mine;
+}
+
+// Merge this chunk's candidates into the running list for E.
+template <int J>
+__device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &sc, const float (&d2)[J], int c0, int E)
+{
+    const int lane = lane_id();
+    const int K = E + 1 + kGuard;
+    const int lo = list_off(E);
+    const int have = sc.lcount[E];
+
+    float mn = CUDART_INF_F;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+        mn = fminf(mn, d2[j]);
+    float srt = warp_sort_asc(mn);
+    float th = __shfl_sync(kFull, srt, K - 1);
+    if (have >= K)
+        th = fminf(th, sc.ld[lo + K - 1]);
+
+    // buffer := current list + chunk candidates with d2 <= th
+    if (lane < have) {
+        sc.cd[lane] = sc.ld[lo + lane];
+        sc.cs[lane] = sc.ls[lo + lane];
+    }
+    if (lane == 0)
+        sc.cnt = have;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        if (d2[j] <= th) {
+            int p = atomicAdd(&sc.cnt, 1);
+            if (p < kCandCap) {
+                sc.cd[p] = d2[j];
+                sc.cs[p] = q.s_first + c0 + lane + 32 * j;
+            }
+        }
+    }
+    __syncwarp();
+    int c = sc.cnt;
+    int tries = 0;
+    while (c > kCandCap) {
+        // Too many at the threshold: tighten it to the K-th smallest key of
+        // the buffered subset (all real candidates) and compact again.
+        unsigned long long kth = buffer_kth_key(sc, kCandCap, K);
+        __syncwarp();
+        if (lane == 0)
+            sc.cnt = 0;
+        __syncwarp();
+        if (lane < have && dkey(sc.ld[lo + lane], sc.ls[lo + lane]) <= kth) {
+            int p = atomicAdd(&sc.cnt, 1);
+            sc.cd[p] = sc.ld[lo + lane];
+            sc.cs[p] = sc.ls[lo + lane];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            int s = q.s_first + c0 + lane + 32 * j;
+            if (d2[j] <= th && dkey(d2[j], s) <= kth) {
+                int p = atomicAdd(&sc.cnt, 1);
+                if (p < kCandCap) {
+                    sc.cd[p] = d2[j];
+                    sc.cs[p] = s;
+                }
+            }
+        }
+        __syncwarp();
+        c = sc.cnt;
+        if (++tries >= 6 && c > kCandCap) {
+            if (lane == 0)
+                sc.ovf[E] = 1;
+            c = kCandCap;
+            break;
+        }
+    }
+    int kept = buffer_to_list(sc, c, K, lo);
+    if (lane == 0)
+        sc.lcount[E] = kept;
+    __syncwarp();
+}
+
+// Exhaustive FP64 selection of the k nearest (rare fallback).
+__device__ __noinline__ void exhaustive64(const KnnQuery q, KnnWarpScratch &sc, int E, int k)
+{
+    const int lane = lane_id();
+    double last_d = -1.0;
+    int last_s = -1;
+    for (int n = 0; n < k; ++n) {
+        double bd = CUDART_INF;
+        int bs = 0x7fffffff;
+        for (int s = q.s_first + lane; s <= q.s_last; s += 32) {
+            if (!cand_ok(q, s, E))
+                continue;
+            double d = dist64(q.xq, q.t, q.xc, s, E, q.tau);
+            bool after = (d > last_d) || (d == last_d && s > last_s);
+            bool better = (d < bd) || (d == bd && s < bs);
+            if (after && better) {
+                bd = d;
+                bs = s;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double od = __shfl_xor_sync(kFull, bd, o);
+            int os = __shfl_xor_sync(kFull, bs, o);
+            if (od < bd || (od == bd && os < bs)) {
+                bd = od;
+                bs = os;
+            }
+        }
+        if (lane == 0) {
+            sc.l64[n] = bd;
+            sc.ls64[n] = bs;
+        }
+        last_d = bd;
+        last_s = bs;
+    }
+    __syncwarp();
+}
+
+// Final neighbours of (query, E) with exact order; lanes n < k receive
+// (s_n, w_n) and call emit(E, k, s_n, w_n, lane < k).
+template <class Emit>
+__device__ __forceinline__ void finalize_E(const KnnQuery &q, KnnWarpScratch &sc, int E, Emit &emit)
+{
+    const int lane = lane_id();
+    const int k = E + 1;
+    const int lo = list_off(E);
+    const int have = sc.lcount[E];
+    const int K = E + 1 + kGuard;
+
+    bool use64 = false;
+    bool full = sc.ovf[E] != 0 || have < k;
+    if (!full) {
+        float Dn = lane < have ? sc.ld[lo + lane] : CUDART_INF_F;
+        float Dn1 = __shfl_down_sync(kFull, Dn, 1);
+        bool ok = true;
+        if (lane < k) {
+            if (lane + 1 < have)
+                ok = (Dn1 - Dn) > d2_err(Dn, E) + d2_err(Dn1, E);
+            else
+                ok = have < K;  // nothing was left out beyond the list
+        }
+        float D0 = __shfl_sync(kFull, Dn, 0);
+        bool all_ok = __all_sync(kFull, ok) && D0 >= kNearDup;
+        if (!all_ok) {
+            // FP64 re-rank of the kept entries.
+            double d64 = CUDART_INF;
+            int s_me = 0;
+            if (lane < have) {
+                s_me = sc.ls[lo + lane];
+                d64 = dist64(q.xq, q.t, q.xc, s_me, E, q.tau);
+            }
+            int r = 0;
+            for (int f = 0; f < have; ++f) {
+                double df = __shfl_sync(kFull, d64, f);
+                int sf = __shfl_sync(kFull, s_me, f);
+                r += (df < d64) || (df == d64 && sf < s_me);
+            }
+            if (lane < have) {
+                sc.l64[r] = d64;
+                sc.ls64[r] = s_me;
+            }
+            __syncwarp();
+            // entries left out have FP32 distance >= the last kept one
+            bool bound_ok = true;
+            if (have >= K) {
+                float Dlast = sc.ld[lo + have - 1];
+                bound_ok = sc.l64[k - 1] < (double)(Dlast - d2_err(Dlast, E));
+            }
+            if (!bound_ok)
+                full = true;
+            use64 = true;
+        }
+    }
+    if (full) {
+        exhaustive64(q, sc, E, k);
+        use64 = true;
+    }
+
+    int s_n = 0;
+    float w = 0.f;
+    if (use64) {
+        double dd = lane < k ? sqrt(sc.l64[lane]) : 0.0;
+        s_n = lane < k ? sc.ls64[lane] : 0;
+        double d1 = __shfl_sync(kFull, dd, 0);
+        double u = 0.0;
+        if (lane < k)
+            u = d1 > 0.0 ? exp(-dd / d1) : (dd == 0.0 ? 1.0 : 0.0);
+        double sum = warp_sum_d(u);
+        w = (float)(u / sum);
+    } else {
+        float dd = lane < k ? sqrtf(sc.ld[lo + lane]) : 0.f;
+        s_n = lane < k ? sc.ls[lo + lane] : 0;
+        float d1 = __shfl_sync(kFull, dd, 0);
+        float u = lane < k ? expf(-dd / d1) : 0.f;
+        float sum = warp_sum(u);
+        w = u / sum;
+    }
+    emit(E, k, s_n, w, lane < k);
+}
+
+// Full query: sweep all candidate chunks, then emit every selected E.
+template <int J, class Emit>
+__device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
+{
+    const int lane = lane_id();
+    for (int E = lane + 1; E <= q.E_lim; E += 32) {
+        sc.lcount[E] = 0;
+        sc.ovf[E] = 0;
+    }
+    __syncwarp();
+    const int n_slots = q.s_last - q.s_first + 1;
+    for (int c0 = 0; c0 < n_slots; c0 += 32 * J) {
+        float d2[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            int s = q.s_first + c0 + lane + 32 * j;
+            d2[j] = cand_ok(q, s, 1) ? 0.f : CUDART_INF_F;
+        }
+        for (int E = 1; E <= q.E_lim; ++E) {
+            const int off = (E - 1) * q.tau;
+            const float xqv = q.xq[q.t - off];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                int s = q.s_first + c0 + lane + 32 * j;
+                int si = s - off;
+                int sc_i = min(max(si, 0), q.s_last);
+                float diff = xqv - q.xc[sc_i];
+                float nd = fmaf(diff, diff, d2[j]);
+                d2[j] = si >= 0 ? nd : CUDART_INF_F;
+            }
+            if ((q.sel >> (E - 1)) & 1u)
+                merge_chunk<J>(q, sc, d2, c0, E);
+        }
+    }
+    for (int E = 1; E <= q.E_lim; ++E)
+        if ((q.sel >> (E - 1)) & 1u)
+            finalize_E(q, sc, E, emit);
+}
+
+}  // namespace edm

@@ -1,0 +1,68 @@
+// launchers.h -- host-side launch helpers shared between the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "edm.h"
+
+namespace edm {
+
+// Shared-memory bytes of the staged series plus per-warp kNN scratch.
+size_t knn_smem_bytes(int T, int warps);
+// Largest T the kNN kernels can stage in shared memory.
+int knn_max_T();
+
+// Phase 1: one CTA per series.  rho_by_E may be null.
+cudaError_t launch_simplex(const float *Y, int64_t N, int T, int64_t ldY, int E_max, int tau, int Tp,
+                           int32_t *optE, float *rho_by_E, cudaStream_t st);
+
+// Internal table layout of one library block (consumed by the lookup).
+struct TableLayout {
+    int64_t lib_stride;             // bytes per library
+    int64_t off_w[EDM_MAX_E + 1];   // byte offset of w[k][Tq_pad] per E (-1: absent)
+    int64_t off_i[EDM_MAX_E + 1];   // byte offset of idx16[k][Tq_pad] per E
+    int Tq_pad;                     // padded row count (multiple of 32)
+};
+
+// Phase 2 tables for n_lib libraries (series lib0 .. lib0+n_lib-1 of Y)
+// for every E whose bit is set in sel, written in the internal layout.
+cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
+                              uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st);
+
+// Public table format: idx int32 [n_lib][Tq][E+1] (unshifted), w float [n_lib][Tq][E+1].
+cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
+                              int32_t *idx, float *w, cudaStream_t st);
+
+// Target tiles: 32 targets of one E, time-major [T][32] float (z-normalised).
+struct TileMeta {
+    int E;
+    int first;  // first sorted position
+    int count;  // targets in this tile (<= 32)
+    int pad;
+};
+
+cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
+                                const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st);
+
+struct LookupArgs {
+    const float *tiles;
+    const TileMeta *meta;
+    const int32_t *pi;
+    const float2 *omom;
+    const uint8_t *tables;
+    TableLayout lay;
+    int T, tau, Tp;
+    int tile_begin, n_tiles;
+    int n_lib;          // libraries in this block
+    int lib_parts;      // grid.y: libraries split into this many parts
+    int64_t rho_col0;   // column of the block's first library in rho
+    float *rho;
+    int64_t ld_rho;
+};
+
+size_t lookup_smem_bytes(int T);
+cudaError_t launch_lookup(const LookupArgs &a, cudaStream_t st);
+
+}  // namespace edm

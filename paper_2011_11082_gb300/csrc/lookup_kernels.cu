@@ -1,0 +1,219 @@
+// lookup_kernels.cu -- target staging and the fused lookup + rho kernel.
+//
+// Lookup (Algorithm 5) and corrcoef for one E-homogeneous tile of 32
+// targets and a block of libraries.  The tile ([T][32] floats, time-major,
+// targets across the 32 banks) sits in shared memory.  A warp serves one
+// library at a time: lane l owns query row t_l = 32b + l of the library's
+// table (its E+1 neighbour offsets and weights stay in registers) and, at
+// step r = 0..31, forms the prediction of target column l^r.  For a fixed
+// r the 32 lanes read 32 different columns, so every gather hits 32
+// distinct banks whatever the neighbour rows are.  Moment sums per
+// (lane, r) are folded into per-target sums through a small shared
+// transpose at the end of the library.
+#include "edm_internal.cuh"
+#include "launchers.h"
+
+namespace edm {
+
+constexpr int kLkWarps = 8;
+constexpr int kLkThreads = kLkWarps * 32;
+constexpr int kRedStride = 33;
+
+// 128 spare bytes let the tile start on a 128-byte boundary of the shared
+// window, which the XOR addressing of the gathers relies on.
+size_t lookup_smem_bytes(int T) { return 128 + (size_t)T * 32 * sizeof(float) + (size_t)kLkWarps * 32 * kRedStride * 4; }
+
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Target staging: z-normalise each target (mean/std over the whole series,
+// FP64), store tiles [T][32], and the per-target observation moments over
+// the window o(t) = z(t+Tp), t in [(E-1)tau, T-1-Tp].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) prep_targets_kernel(const float *__restrict__ Y, int64_t ldY, int T, int tau,
+                                                           int Tp, const int32_t *__restrict__ pi,
+                                                           const TileMeta *__restrict__ meta, float *__restrict__ tiles,
+                                                           float2 *__restrict__ omom)
+{
+    __shared__ float mu_s[32], inv_s[32];
+    const TileMeta m = meta[blockIdx.x];
+    const int lane = lane_id(), warp = warp_id();
+    for (int slot = warp; slot < 32; slot += 8) {
+        double mu = 0.0, inv = 0.0;
+        if (slot < m.count) {
+            const float *y = Y + (int64_t)pi[m.first + slot] * ldY;
+            double a = 0.0;
+            for (int t = lane; t < T; t += 32)
+                a += (double)y[t];
+            mu = warp_sum_d(a) / (double)T;
+            double v = 0.0;
+            for (int t = lane; t < T; t += 32) {
+                double d = (double)y[t] - mu;
+                v += d * d;
+            }
+            v = warp_sum_d(v) / (double)T;
+            inv = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+            // observation moments of the staged (float) values
+            const float muf = (float)mu, invf = (float)inv;
+            const int L = (m.E - 1) * tau;
+            double so = 0.0, soo = 0.0;
+            for (int t = L + Tp + lane; t < T; t += 32) {
+                float z = (y[t] - muf) * invf;
+                so += (double)z;
+                soo += (double)z * (double)z;
+            }
+            so = warp_sum_d(so);
+            soo = warp_sum_d(soo);
+            if (lane == 0) {
+                double n = (double)(T - Tp - L);
+                omom[m.first + slot] = make_float2((float)so, (float)(n * soo - so * so));
+            }
+        }
+        if (lane == 0) {
+            mu_s[slot] = (float)mu;
+            inv_s[slot] = (float)inv;
+        }
+    }
+    __syncthreads();
+    float *tile = tiles + (size_t)blockIdx.x * T * 32;
+    const int slot = lane;
+    const float *y = slot < m.count ? Y + (int64_t)pi[m.first + slot] * ldY : nullptr;
+    const float muf = mu_s[slot], invf = inv_s[slot];
+    for (int t = warp; t < T; t += 8) {
+        float z = y ? (y[t] - muf) * invf : 0.f;
+        tile[(size_t)t * 32 + slot] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lookup + rho.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kLkThreads, 1) lookup_kernel(LookupArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t pad = (128u - (raw & 127u)) & 127u;
+    unsigned char *smem = smem_raw + pad;
+    float *tile_s = reinterpret_cast<float *>(smem);
+    float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * 32 * sizeof(float));
+    const uint32_t base = raw + pad;
+
+    const int tile = a.tile_begin + blockIdx.x;
+    const TileMeta m = a.meta[tile];
+    const int E = m.E, k = E + 1;
+    const int L = (E - 1) * a.tau;
+    const int Tq = a.T - a.Tp - L;
+    const int nblk = (Tq + 31) / 32;
+
+    {  // stage the tile
+        const float4 *src = reinterpret_cast<const float4 *>(a.tiles + (size_t)tile * a.T * 32);
+        float4 *dst = reinterpret_cast<float4 *>(tile_s);
+        const int n4 = a.T * 8;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x)
+            dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+
+    const int lane = lane_id(), warp = warp_id();
+    float *red = red_all + warp * 32 * kRedStride;
+    const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
+    const int lib_lo = blockIdx.y * per;
+    const int lib_hi = min(a.n_lib, lib_lo + per);
+    const uint32_t lane4 = (uint32_t)lane * 4u;
+
+    for (int lib = lib_lo + warp; lib < lib_hi; lib += kLkWarps) {
+        const uint8_t *lb = a.tables + (size_t)lib * a.lay.lib_stride;
+        const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
+        const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        float Sp[32], Spp[32], Spo[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            Sp[r] = 0.f;
+            Spp[r] = 0.f;
+            Spo[r] = 0.f;
+        }
+        for (int b = 0; b < nblk; ++b) {
+            const int row = b * 32 + lane;
+            const bool valid = row < Tq;
+            float p[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                p[r] = 0.f;
+            for (int n = 0; n < k; ++n) {
+                float wv = 0.f;
+                uint32_t iv = 0;
+                if (valid) {
+                    wv = __ldg(Wt + (size_t)n * a.lay.Tq_pad + row);
+                    iv = __ldg(It + (size_t)n * a.lay.Tq_pad + row);
+                }
+                const uint32_t A = base + iv * 128u + lane4;
+#pragma unroll
+                for (int r = 0; r < 32; ++r)
+                    p[r] = fmaf(wv, lds_f32(A ^ (uint32_t)(r * 4)), p[r]);
+            }
+            const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
+            const uint32_t Ao = base + orow * 128u + lane4;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                float o = lds_f32(Ao ^ (uint32_t)(r * 4));
+                Sp[r] += p[r];
+                Spp[r] = fmaf(p[r], p[r], Spp[r]);
+                Spo[r] = fmaf(p[r], o, Spo[r]);
+            }
+        }
+        // per-target sums: target c collects slot c^l of every lane l
+        float tot[3];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) {
+            const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                red[r * kRedStride + lane] = S[r];
+            __syncwarp();
+            float s = 0.f;
+#pragma unroll
+            for (int l2 = 0; l2 < 32; ++l2)
+                s += red[(lane ^ l2) * kRedStride + l2];
+            tot[mm] = s;
+            __syncwarp();
+        }
+        if (lane < m.count) {
+            const int64_t j = a.pi[m.first + lane];
+            const float2 om = a.omom[m.first + lane];
+            const float n = (float)Tq;
+            const float num = n * tot[2] - tot[0] * om.x;
+            const float den_p = n * tot[1] - tot[0] * tot[0];
+            const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;
+            a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho;
+        }
+    }
+}
+
+cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
+                                const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st)
+{
+    if (n_tiles <= 0)
+        return cudaSuccess;
+    prep_targets_kernel<<<n_tiles, 256, 0, st>>>(Y, ldY, T, tau, Tp, pi, meta, tiles, omom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lookup(const LookupArgs &a, cudaStream_t st)
+{
+    if (a.n_tiles <= 0 || a.n_lib <= 0)
+        return cudaSuccess;
+    size_t smem = lookup_smem_bytes(a.T);
+    cudaError_t e = cudaFuncSetAttribute(lookup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
+    lookup_kernel<<<grid, kLkThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace edm

@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads and exports every symbol of include/edm.h;
+argument checks and size queries work without a GPU (no compute calls)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "edm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(edm_[a-zA-Z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2011_11082_gb300 import _abi
+
+    return _abi.load()
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for required in ("edm_optimal_E", "edm_knn_table", "edm_ccm_rho", "edm_ccm_workspace_bytes",
+                     "edm_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2011_11082_gb300 import _abi
+
+    raw = ctypes.CDLL(_abi.lib_path())
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+        assert name in _abi.SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings_and_version(lib):
+    assert lib.edm_status_string(0) == b"EDM_OK"
+    assert b"INVALID" in lib.edm_status_string(1)
+    assert lib.edm_version() >= 0x000100
+
+
+def test_argument_checks_need_no_gpu(lib):
+    from paper_2011_11082_gb300 import make_params
+
+    p = make_params(E_max=10)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: checks fail first
+    # null pointers
+    assert lib.edm_optimal_E(None, 4, 100, 100, ctypes.byref(p), None, None, None) == 1
+    # T too short for E_max
+    assert lib.edm_optimal_E(fake, 4, 30, 30, ctypes.byref(p), fake, None, None) == 1
+    # E_max beyond the build limit
+    p2 = make_params(E_max=21)
+    assert lib.edm_optimal_E(fake, 4, 1000, 1000, ctypes.byref(p2), fake, None, None) == 5
+    # bad tau / Tp / exclusion radius
+    for bad in (make_params(tau=0), make_params(Tp=-1), make_params(exclusion_radius=-2)):
+        assert lib.edm_optimal_E(fake, 4, 1000, 1000, ctypes.byref(bad), fake, None, None) == 1
+    # knn: Tq inconsistent with T, E
+    assert lib.edm_knn_table(fake, 2, 100, 100, 3, ctypes.byref(p), fake, fake, 50, None) == 1
+    # ccm: library range outside [0, N), ld_rho too small, workspace too small
+    ws_need = lib.edm_ccm_workspace_bytes(64, 500, ctypes.byref(p))
+    assert ws_need > 0
+    assert lib.edm_ccm_rho(fake, 64, 500, 500, fake, 60, 10, ctypes.byref(p), fake, 64, fake, ws_need, None) == 1
+    assert lib.edm_ccm_rho(fake, 64, 500, 500, fake, 0, 64, ctypes.byref(p), fake, 32, fake, ws_need, None) == 1
+    assert lib.edm_ccm_rho(fake, 64, 500, 500, fake, 0, 64, ctypes.byref(p), fake, 64, fake, ws_need - 1, None) == 3
+
+
+def test_workspace_grows_with_problem(lib):
+    from paper_2011_11082_gb300 import make_params
+
+    p = make_params()
+    a = lib.edm_ccm_workspace_bytes(1000, 1500, ctypes.byref(p))
+    b = lib.edm_ccm_workspace_bytes(100000, 1500, ctypes.byref(p))
+    assert b > a > 1000 * 1500 * 4

@@ -1,0 +1,168 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: neighbour indices bit-exact; optimal E identical; rho within 1e-4
+absolute (weights within 1e-6).  Sizes span several tiles and ragged tails.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import edm_synth as synth
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+RHO_TOL = 1e-4
+W_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def edm():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2011_11082_gb300 as m
+
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _tie_series(T):
+    """Series with exact distance ties (integer-period sine, a step pattern)."""
+    s = synth.sine_series(T, 16)
+    step = (np.arange(T) % 7).astype(np.float32) - 3.0
+    return np.stack([s, step])
+
+
+@pytest.mark.parametrize("E", [1, 2, 3, 5, 8, 13, 20])
+def test_knn_tables_bit_exact(edm, E):
+    Y = np.concatenate([synth.coupled_logistic(6, 500, 0.05, 0.05, seed_data=3, seed_noise=4), _tie_series(500)])
+    Yd = _dev(Y)
+    for tau, Tp, excl in ((1, 1, 0), (2, 1, 3), (1, 0, 0), (1, 2, -1)):
+        idx, w = edm.edm_knn_table(Yd, E, tau=tau, Tp=Tp, exclusion_radius=excl)
+        idx, w = idx.cpu().numpy(), w.cpu().numpy()
+        for i in range(Y.shape[0]):
+            oi, ow = orc.ccm_table(Y[i], E, tau, Tp, excl)
+            assert np.array_equal(idx[i], oi), (E, tau, Tp, excl, i, np.argwhere(idx[i] != oi)[:5])
+            assert np.abs(w[i] - ow).max() < W_TOL, (E, tau, Tp, excl, i)
+
+
+def test_knn_tables_long_series_chunked(edm):
+    """T = 3000 exceeds one candidate chunk per lane (chunked path)."""
+    Y = synth.coupled_logistic(3, 3000, 0.1, 0.05, seed_data=5, seed_noise=6)
+    Yd = _dev(Y)
+    for E in (2, 7):
+        idx, w = edm.edm_knn_table(Yd, E)
+        idx, w = idx.cpu().numpy(), w.cpu().numpy()
+        for i in range(3):
+            oi, ow = orc.ccm_table(Y[i], E)
+            assert np.array_equal(idx[i], oi)
+            assert np.abs(w[i] - ow).max() < W_TOL
+
+
+def test_optimal_E_small_workload(edm):
+    Y = synth.workload("n64_t500")
+    optE, rho = edm.edm_optimal_E(_dev(Y), E_max=10)
+    oE, orho = orc.optimal_E(Y, 10)
+    assert np.array_equal(optE.cpu().numpy(), oE)
+    assert np.nanmax(np.abs(rho.cpu().numpy() - orho)) < 2e-5
+
+
+def test_optimal_E_n2048_sample(edm):
+    Y = synth.workload("n2048_t1500")
+    optE, rho = edm.edm_optimal_E(_dev(Y), E_max=20)
+    sel = np.random.default_rng(0).choice(Y.shape[0], 192, replace=False)
+    oE, orho = orc.optimal_E(Y[sel], 20)
+    got = optE.cpu().numpy()[sel]
+    bad = np.nonzero(got != oE)[0]
+    assert bad.size == 0, [(int(sel[b]), int(got[b]), int(oE[b]), orho[b]) for b in bad[:3]]
+    assert np.nanmax(np.abs(rho.cpu().numpy()[sel] - orho)) < 2e-5
+
+
+def test_optimal_E_odd_T_tau2(edm):
+    Y = synth.coupled_logistic(40, 401, 0.05, 0.05, seed_data=9, seed_noise=10)
+    optE, rho = edm.edm_optimal_E(_dev(Y), E_max=8, tau=2, Tp=2)
+    oE, orho = orc.optimal_E(Y, 8, tau=2, Tp=2)
+    assert np.array_equal(optE.cpu().numpy(), oE)
+    assert np.nanmax(np.abs(rho.cpu().numpy() - orho)) < 2e-5
+
+
+def test_ccm_full_small_workload(edm):
+    Y = synth.workload("n64_t500")
+    oE, _ = orc.optimal_E(Y, 10)
+    rho_t = edm.edm_ccm_rho(_dev(Y), torch.from_numpy(oE).cuda())
+    R = orc.ccm_rho_rows(Y, oE)
+    got = rho_t.t().cpu().numpy()
+    assert np.abs(got - R).max() < RHO_TOL
+
+
+def test_ccm_n2048_sampled_rows(edm):
+    Y = synth.workload("n2048_t1500")
+    Yd = _dev(Y)
+    optE, _ = edm.edm_optimal_E(Yd, E_max=20)
+    rho_t = edm.edm_ccm_rho(Yd, optE)
+    oE = optE.cpu().numpy()
+    rows = np.random.default_rng(1).choice(Y.shape[0], 12, replace=False)
+    R = orc.ccm_rho_rows(Y, oE, rows=rows)
+    got = rho_t.cpu().numpy()[:, rows].T
+    assert np.abs(got - R).max() < RHO_TOL
+
+
+def test_ccm_ragged_and_subranges(edm):
+    Y = synth.coupled_logistic(37, 260, 0.05, 0.05, seed_data=11, seed_noise=12)
+    rng = np.random.default_rng(2)
+    oE = rng.integers(1, 7, size=37).astype(np.int32)
+    R = orc.ccm_rho_rows(Y, oE)
+    Yd, Ed = _dev(Y), torch.from_numpy(oE).cuda()
+    full = edm.edm_ccm_rho(Yd, Ed).cpu().numpy().T
+    assert np.abs(full - R).max() < RHO_TOL
+    # a library sub-range written into a wider buffer
+    out = torch.full((37, 20), float("nan"), device="cuda")
+    edm.edm_ccm_rho(Yd, Ed, lib_begin=9, lib_count=13, out=out)
+    blk = out.cpu().numpy()
+    assert np.abs(blk[:, :13].T - R[9:22]).max() < RHO_TOL
+    assert np.isnan(blk[:, 13:]).all()
+
+
+def test_ccm_single_series_and_uniform_E(edm):
+    Y = synth.coupled_logistic(1, 120, 0.0, 0.0, seed_data=13, seed_noise=14)
+    for E in (1, 4):
+        oE = np.array([E], np.int32)
+        got = edm.edm_ccm_rho(_dev(Y), torch.from_numpy(oE).cuda()).cpu().numpy()
+        assert abs(got[0, 0] - orc.ccm_rho_rows(Y, oE)[0, 0]) < RHO_TOL
+
+
+def test_ccm_tau_Tp_exclusion_variants(edm):
+    Y = synth.coupled_logistic(20, 300, 0.05, 0.05, seed_data=15, seed_noise=16)
+    oE = np.random.default_rng(3).integers(1, 6, size=20).astype(np.int32)
+    for tau, Tp, excl in ((2, 1, 0), (1, 2, 5), (1, 0, -1)):
+        R = orc.ccm_rho_rows(Y, oE, tau=tau, Tp=Tp, excl=excl)
+        got = edm.edm_ccm_rho(_dev(Y), torch.from_numpy(oE).cuda(), tau=tau, Tp=Tp,
+                              exclusion_radius=excl).cpu().numpy().T
+        assert np.abs(got - R).max() < RHO_TOL, (tau, Tp, excl)
+
+
+def test_ccm_closed_forms(edm):
+    """Integer-period sine predicts itself exactly; self-inclusion gives 1."""
+    T = 400
+    x = synth.sine_series(T, 16)
+    c = np.cos(2 * np.pi * np.mod(np.arange(T), 16) / 16).astype(np.float32)
+    Y = np.stack([x, c])
+    got = edm.edm_ccm_rho(_dev(Y), torch.tensor([3, 3], dtype=torch.int32, device="cuda")).cpu().numpy()
+    assert np.abs(got - 1.0).max() < 1e-5
+    L = synth.logistic_series(300)[None, :]
+    got = edm.edm_ccm_rho(_dev(L), torch.tensor([2], dtype=torch.int32, device="cuda"), Tp=0,
+                          exclusion_radius=-1).cpu().numpy()
+    assert abs(got[0, 0] - 1.0) < 1e-6
+
+
+def test_ccm_deterministic(edm):
+    Y = synth.coupled_logistic(70, 350, 0.05, 0.05, seed_data=17, seed_noise=18)
+    Yd = _dev(Y)
+    optE, _ = edm.edm_optimal_E(Yd, E_max=8)
+    a = edm.edm_ccm_rho(Yd, optE).cpu().numpy()
+    b = edm.edm_ccm_rho(Yd, optE).cpu().numpy()
+    assert np.array_equal(a, b, equal_nan=True)
