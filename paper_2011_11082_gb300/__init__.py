@@ -43,6 +43,11 @@ def _stream(stream=None) -> int:
     return int(s.cuda_stream)
 
 
+def _ld(t: torch.Tensor) -> int:
+    """Row pitch in elements (a single row's stride is meaningless)."""
+    return int(t.stride(0)) if t.shape[0] > 1 else int(t.shape[1])
+
+
 def _dev_f32(Y: torch.Tensor, name: str) -> torch.Tensor:
     if not (isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dtype == torch.float32):
         raise TypeError(f"{name} must be a float32 CUDA tensor")
@@ -60,7 +65,7 @@ def edm_optimal_E(Y: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, r
     optE = torch.empty(N, dtype=torch.int32, device=Y.device)
     rho = torch.empty((N, E_max), dtype=torch.float32, device=Y.device) if return_rho else None
     p = make_params(E_max=E_max, tau=tau, Tp=Tp)
-    st = lib.edm_optimal_E(Y.data_ptr(), N, T, Y.stride(0), ctypes.byref(p), optE.data_ptr(),
+    st = lib.edm_optimal_E(Y.data_ptr(), N, T, _ld(Y), ctypes.byref(p), optE.data_ptr(),
                            rho.data_ptr() if rho is not None else None, _stream(stream))
     _abi.check(st, "edm_optimal_E")
     return optE, rho
@@ -78,7 +83,7 @@ def edm_knn_table(Y: torch.Tensor, E: int, tau: int = 1, Tp: int = 1, exclusion_
     idx = torch.empty((n, Tq, E + 1), dtype=torch.int32, device=Y.device)
     w = torch.empty((n, Tq, E + 1), dtype=torch.float32, device=Y.device)
     p = make_params(E_max=E, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius)
-    st = lib.edm_knn_table(Y.data_ptr(), n, T, Y.stride(0), E, ctypes.byref(p), idx.data_ptr(), w.data_ptr(), Tq,
+    st = lib.edm_knn_table(Y.data_ptr(), n, T, _ld(Y), E, ctypes.byref(p), idx.data_ptr(), w.data_ptr(), Tq,
                            _stream(stream))
     _abi.check(st, "edm_knn_table")
     return idx, w
@@ -114,8 +119,8 @@ def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_cou
     need = int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)
-    st = lib.edm_ccm_rho(Y.data_ptr(), N, T, Y.stride(0), optE.data_ptr(), lib_begin, lib_count, ctypes.byref(p),
-                         out.data_ptr(), out.stride(0), workspace.data_ptr(), workspace.numel(), _stream(stream))
+    st = lib.edm_ccm_rho(Y.data_ptr(), N, T, _ld(Y), optE.data_ptr(), lib_begin, lib_count, ctypes.byref(p),
+                         out.data_ptr(), _ld(out), workspace.data_ptr(), workspace.numel(), _stream(stream))
     _abi.check(st, "edm_ccm_rho")
     return out
 

@@ -346,31 +346,37 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
                 EDM_CUDA(edm::launch_knn_tables(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
                                                 params->exclusion_radius, sel, lay, tables_d, st));
             }
-            edm::LookupArgs a;
-            a.tiles = tiles_d;
-            a.meta = meta_d;
-            a.pi = pi_d;
-            a.omom = omom_d;
-            a.tables = tables_d;
-            a.lay = lay;
-            a.T = (int)T;
-            a.tau = params->tau;
-            a.Tp = params->Tp;
-            a.tile_begin = tb0;
-            a.n_tiles = ntb;
-            a.n_lib = nlb;
-            int parts = (4 * sms + ntb - 1) / ntb;
-            parts = std::max(1, std::min(parts, (nlb + 7) / 8));
-            a.lib_parts = parts;
-            a.rho_col0 = lb0;
-            a.rho = rho;
-            a.ld_rho = ld_rho;
-            {
+            // one launch per run of equal E inside the target block
+            for (int r0 = tb0; r0 < tb0 + ntb;) {
+                const int E = tiles[(size_t)r0].E;
+                int r1 = r0;
                 int64_t targets = 0;
-                for (int t = tb0; t < tb0 + ntb; ++t)
-                    targets += tiles[(size_t)t].count;
-                LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                EDM_CUDA(edm::launch_lookup(a, st));
+                while (r1 < tb0 + ntb && tiles[(size_t)r1].E == E)
+                    targets += tiles[(size_t)r1++].count;
+                edm::LookupArgs a;
+                a.tiles = tiles_d;
+                a.meta = meta_d;
+                a.pi = pi_d;
+                a.omom = omom_d;
+                a.tables = tables_d;
+                a.lay = lay;
+                a.T = (int)T;
+                a.tau = params->tau;
+                a.Tp = params->Tp;
+                a.tile_begin = r0;
+                a.n_tiles = r1 - r0;
+                a.n_lib = nlb;
+                int parts = (4 * sms + a.n_tiles - 1) / a.n_tiles;
+                parts = std::max(1, std::min(parts, (nlb + 7) / 8));
+                a.lib_parts = parts;
+                a.rho_col0 = lb0;
+                a.rho = rho;
+                a.ld_rho = ld_rho;
+                {
+                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
+                    EDM_CUDA(edm::launch_lookup(a, E, st));
+                }
+                r0 = r1;
             }
         }
     }

@@ -7,10 +7,15 @@
 // over the candidates serves every E in 1..E_lim; a bit mask selects the E
 // whose neighbour lists are wanted (Sec. III-B: one table per E, Algorithm 2).
 //
-// Selection per (query, E): the K-th smallest of the 32 lane minima is an
-// upper bound on the K-th smallest distance (K = E+1+kGuard), so only the
-// few candidates at or below it are compacted into a shared buffer, ranked
-// by (d2, s) and kept as a sorted list that carries over to the next chunk.
+// Selection per (query, E), K = E+1+kGuard: a threshold th that at least K
+// real candidates meet is found cheaply -- from the previous E's list (each
+// of its entries' distance grows by one lag, recomputed in the same FP32
+// order as the lanes), from this E's list of earlier chunks, or, for the
+// first E, as the K-th smallest of the 32 lane minima.  Only the few
+// candidates at or below th are compacted (one ballot per register slot),
+// ranked by (d2, s) and kept as a sorted list carried to the next chunk.
+// The list stores K+1 entries: the first K are the exact K smallest; the
+// extra one is a real candidate that lets the next E seed its threshold.
 //
 // Exactness (neighbours identical to the FP64 reference): the FP32 sum has a
 // known error bound (d2_err).  When every gap among the first E+2 entries
@@ -24,7 +29,8 @@
 
 namespace edm {
 
-__host__ __device__ constexpr int list_off(int E) { return (E - 1) * E / 2 + (E - 1) * (1 + kGuard); }
+// list capacity for E is E + 2 + kGuard (= K + 1)
+__host__ __device__ constexpr int list_off(int E) { return (E - 1) * E / 2 + (E - 1) * (2 + kGuard); }
 constexpr int kListTotal = list_off(EDM_MAX_E + 1);
 
 struct KnnWarpScratch {
@@ -42,7 +48,8 @@ struct KnnWarpScratch {
 
 struct KnnQuery {
     const float *xq;  // query series (shared memory)
-    const float *xc;  // candidate series (shared memory)
+    const float *xc;  // candidate series (shared memory); readable from
+                      // xc[-(E_lim-1)*tau] to xc[s_first + 32*J*chunks - 1]
     int t;            // query time in xq
     int s_first;      // first candidate time (slot 0)
     int s_last;       // last candidate time
@@ -73,11 +80,28 @@ __device__ __forceinline__ bool cand_ok(const KnnQuery &q, int s, int E)
     return true;
 }
 
-// Rank-select: the buffer holds c (<= kCandCap) entries; write the K
-// smallest by (d, s) in order into the list for E.  Returns the count kept.
-__device__ __forceinline__ int buffer_to_list(KnnWarpScratch &sc, int c, int K, int lo)
+// Rank-select: the buffer holds c (<= kCandCap) entries; write the cap
+// smallest by (d, s) in order into the list at lo.  Returns the count kept.
+__device__ __forceinline__ int buffer_to_list(KnnWarpScratch &sc, int c, int cap, int lo)
 {
     const int lane = lane_id();
+    if (c <= 32) {
+        float d0 = lane < c ? sc.cd[lane] : CUDART_INF_F;
+        int s0 = lane < c ? sc.cs[lane] : 0x7fffffff;
+        int r0 = 0;
+        for (int f = 0; f < c; ++f) {
+            float df = __shfl_sync(kFull, d0, f);
+            int sf = __shfl_sync(kFull, s0, f);
+            r0 += (df < d0) || (df == d0 && sf < s0);
+        }
+        __syncwarp();
+        if (lane < c && r0 < cap) {
+            sc.ld[lo + r0] = d0;
+            sc.ls[lo + r0] = s0;
+        }
+        __syncwarp();
+        return c < cap ? c : cap;
+    }
     unsigned long long k0 = ~0ull, k1 = ~0ull;
     float d0 = 0.f, d1 = 0.f;
     int s0 = 0, s1 = 0;
@@ -98,16 +122,16 @@ __device__ __forceinline__ int buffer_to_list(KnnWarpScratch &sc, int c, int K, 
         r1 += kf < k1;
     }
     __syncwarp();
-    if (lane < c && r0 < K) {
+    if (lane < c && r0 < cap) {
         sc.ld[lo + r0] = d0;
         sc.ls[lo + r0] = s0;
     }
-    if (lane + 32 < c && r1 < K) {
+    if (lane + 32 < c && r1 < cap) {
         sc.ld[lo + r1] = d1;
         sc.ls[lo + r1] = s1;
     }
     __syncwarp();
-    return c < K ? c : K;
+    return c < cap ? c : cap;
 }
 
 // K-th smallest key among the first c buffered entries (c > K).
@@ -136,44 +160,73 @@ __device__ __forceinline__ unsigned long long buffer_kth_key(KnnWarpScratch &sc,
     return mine;
 }
 
-// Merge this chunk's candidates into the running list for E.
+// Merge this chunk's candidates into the running list for E.  prevE is the
+// last E (< E) whose list was updated in this chunk, or 0.
 template <int J>
-__device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &sc, const float (&d2)[J], int c0, int E)
+__device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &sc, const float (&d2)[J], int c0, int E,
+                                            int prevE)
 {
     const int lane = lane_id();
     const int K = E + 1 + kGuard;
+    const int cap = K + 1;
     const int lo = list_off(E);
     const int have = sc.lcount[E];
 
-    float mn = CUDART_INF_F;
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-        mn = fminf(mn, d2[j]);
-    float srt = warp_sort_asc(mn);
-    float th = __shfl_sync(kFull, srt, K - 1);
+    float th = CUDART_INF_F;
     if (have >= K)
-        th = fminf(th, sc.ld[lo + K - 1]);
+        th = sc.ld[lo + K - 1];
+    if (prevE > 0 && sc.lcount[prevE] >= K) {
+        // grow the previous list's distances to dimension E (same FP32 order)
+        const int plo = list_off(prevE);
+        float dv = 0.f;
+        if (lane < K) {
+            dv = sc.ld[plo + lane];
+            const int sv = sc.ls[plo + lane];
+            if (sv < (E - 1) * q.tau) {
+                dv = CUDART_INF_F;  // not embeddable at E: not a candidate
+            } else {
+                for (int m = prevE; m < E; ++m) {
+                    float diff = q.xq[q.t - m * q.tau] - q.xc[sv - m * q.tau];
+                    dv = fmaf(diff, diff, dv);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            dv = fmaxf(dv, __shfl_xor_sync(kFull, dv, o));
+        th = fminf(th, dv);
+    }
+    if (th == CUDART_INF_F) {
+        float mn = CUDART_INF_F;
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            mn = fminf(mn, d2[j]);
+        float srt = warp_sort_asc(mn);
+        th = __shfl_sync(kFull, srt, K - 1);
+    }
 
-    // buffer := current list + chunk candidates with d2 <= th
+    // buffer := current list + chunk candidates with d2 <= th (ballot per slot)
     if (lane < have) {
         sc.cd[lane] = sc.ld[lo + lane];
         sc.cs[lane] = sc.ls[lo + lane];
     }
-    if (lane == 0)
-        sc.cnt = have;
-    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = have;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        if (d2[j] <= th) {
-            int p = atomicAdd(&sc.cnt, 1);
-            if (p < kCandCap) {
-                sc.cd[p] = d2[j];
-                sc.cs[p] = q.s_first + c0 + lane + 32 * j;
+        const bool p = d2[j] <= th;
+        const unsigned b = __ballot_sync(kFull, p);
+        if (b) {
+            const int pos = base + __popc(b & lt);
+            if (p && pos < kCandCap) {
+                sc.cd[pos] = d2[j];
+                sc.cs[pos] = q.s_first + c0 + lane + 32 * j;
             }
+            base += __popc(b);
         }
     }
     __syncwarp();
-    int c = sc.cnt;
+    int c = base;
     int tries = 0;
     while (c > kCandCap) {
         // Too many at the threshold: tighten it to the K-th smallest key of
@@ -209,7 +262,7 @@ __device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &s
             break;
         }
     }
-    int kept = buffer_to_list(sc, c, K, lo);
+    int kept = buffer_to_list(sc, c, cap, lo);
     if (lane == 0)
         sc.lcount[E] = kept;
     __syncwarp();
@@ -262,8 +315,8 @@ __device__ __forceinline__ void finalize_E(const KnnQuery &q, KnnWarpScratch &sc
     const int lane = lane_id();
     const int k = E + 1;
     const int lo = list_off(E);
-    const int have = sc.lcount[E];
     const int K = E + 1 + kGuard;
+    const int have = min(sc.lcount[E], K);
 
     bool use64 = false;
     bool full = sc.ovf[E] != 0 || have < k;
@@ -354,20 +407,29 @@ __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
             int s = q.s_first + c0 + lane + 32 * j;
             d2[j] = cand_ok(q, s, 1) ? 0.f : CUDART_INF_F;
         }
+        int prevE = 0;
         for (int E = 1; E <= q.E_lim; ++E) {
             const int off = (E - 1) * q.tau;
             const float xqv = q.xq[q.t - off];
+            // reads before the series start land in its zero padding; those
+            // candidates are not embeddable at this E and are dropped below
+            const float *xcj = q.xc + (q.s_first + c0 + lane - off);
 #pragma unroll
             for (int j = 0; j < J; ++j) {
-                int s = q.s_first + c0 + lane + 32 * j;
-                int si = s - off;
-                int sc_i = min(max(si, 0), q.s_last);
-                float diff = xqv - q.xc[sc_i];
-                float nd = fmaf(diff, diff, d2[j]);
-                d2[j] = si >= 0 ? nd : CUDART_INF_F;
+                float diff = xqv - xcj[32 * j];
+                d2[j] = fmaf(diff, diff, d2[j]);
             }
-            if ((q.sel >> (E - 1)) & 1u)
-                merge_chunk<J>(q, sc, d2, c0, E);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                if (q.s_first + c0 + 32 * j >= off)
+                    break;
+                if (q.s_first + c0 + lane + 32 * j < off)
+                    d2[j] = CUDART_INF_F;
+            }
+            if ((q.sel >> (E - 1)) & 1u) {
+                merge_chunk<J>(q, sc, d2, c0, E, prevE);
+                prevE = E;
+            }
         }
     }
     for (int E = 1; E <= q.E_lim; ++E)

@@ -10,13 +10,35 @@ namespace edm {
 constexpr int kKnnWarps = 8;
 constexpr int kKnnThreads = kKnnWarps * 32;
 
+// The staged series is padded: `front` zeros before it (reads of lags
+// before the series start) and 32*J + 4 after it (the tail of the last
+// candidate chunk).  front is a multiple of 4 floats.
+static int front_pad(int E_hi, int tau) { return ((E_hi - 1) * tau + 3) & ~3; }
+
+__host__ __device__ static size_t series_floats(int T, int front, int J) { return ((size_t)front + T + 32 * J + 4 + 3) & ~(size_t)3; }
+
 size_t knn_smem_bytes(int T, int warps)
 {
-    size_t series = ((size_t)T * sizeof(float) + 15) & ~(size_t)15;
-    return series + (size_t)warps * sizeof(KnnWarpScratch) + 64;
+    // worst case: J = 48, front for E = EDM_MAX_E at tau = 1 (larger tau is
+    // sized at launch)
+    return series_floats(T, front_pad(EDM_MAX_E, 1), 48) * sizeof(float) + (size_t)warps * sizeof(KnnWarpScratch) + 64;
 }
 
-int knn_max_T() { return (int)((200 * 1024 - kKnnWarps * sizeof(KnnWarpScratch) - 64) / sizeof(float)); }
+static size_t knn_smem_bytes_exact(int T, int front, int J)
+{
+    return series_floats(T, front, J) * sizeof(float) + (size_t)kKnnWarps * sizeof(KnnWarpScratch) + 64;
+}
+
+int knn_max_T() { return (int)((200 * 1024 - kKnnWarps * sizeof(KnnWarpScratch) - 64) / sizeof(float)) - 32 * 48 - 1024; }
+
+// Stage series `src` (T floats) into xs[-front .. T + tail) with zero pads.
+__device__ __forceinline__ void stage_series(float *xs_base, const float *__restrict__ src, int T, int front, int total)
+{
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        int t = i - front;
+        xs_base[i] = (t >= 0 && t < T) ? src[t] : 0.f;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Phase 1: simplex projection of every series over E = 1..E_max.
@@ -58,22 +80,21 @@ struct SimplexEmit {
 };
 
 template <int J>
-__global__ void __launch_bounds__(kKnnThreads) simplex_kernel(const float *__restrict__ Y, int64_t ldY, int T,
-                                                              int E_max, int tau, int Tp, int32_t *__restrict__ optE,
-                                                              float *__restrict__ rho_by_E)
+__global__ void __launch_bounds__(kKnnThreads, 2) simplex_kernel(const float *__restrict__ Y, int64_t ldY, int T,
+                                                                 int E_max, int tau, int Tp, int front,
+                                                                 int32_t *__restrict__ optE,
+                                                                 float *__restrict__ rho_by_E)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *x = reinterpret_cast<float *>(smem);
-    size_t series_bytes = ((size_t)T * sizeof(float) + 15) & ~(size_t)15;
-    KnnWarpScratch *scratch = reinterpret_cast<KnnWarpScratch *>(smem + series_bytes);
+    const int total = (int)series_floats(T, front, J);
+    float *x = reinterpret_cast<float *>(smem) + front;
+    KnnWarpScratch *scratch = reinterpret_cast<KnnWarpScratch *>(smem + (size_t)total * sizeof(float));
     __shared__ double red[kKnnWarps][EDM_MAX_E][5];
     __shared__ double shift_sh;
     __shared__ double rho_sh[EDM_MAX_E];
 
     const int64_t i = blockIdx.x;
-    const float *src = Y + i * ldY;
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        x[t] = src[t];
+    stage_series(reinterpret_cast<float *>(smem), Y + i * ldY, T, front, total);
     __syncthreads();
 
     // shift for the moments: the series mean (Pearson is shift invariant)
@@ -201,20 +222,18 @@ struct EmitPublic {
 };
 
 template <int J, bool kPublic>
-__global__ void __launch_bounds__(kKnnThreads)
+__global__ void __launch_bounds__(kKnnThreads, 2)
     knn_tables_kernel(const float *__restrict__ Y, int64_t ldY, int64_t lib0, int T, int tau, int Tp, int excl,
-                      uint32_t sel, int q_per_cta, TableLayout lay, uint8_t *__restrict__ tables,
+                      uint32_t sel, int q_per_cta, int front, TableLayout lay, uint8_t *__restrict__ tables,
                       int32_t *__restrict__ pub_idx, float *__restrict__ pub_w, int pub_E)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *x = reinterpret_cast<float *>(smem);
-    size_t series_bytes = ((size_t)T * sizeof(float) + 15) & ~(size_t)15;
-    KnnWarpScratch *scratch = reinterpret_cast<KnnWarpScratch *>(smem + series_bytes);
+    const int total = (int)series_floats(T, front, J);
+    float *x = reinterpret_cast<float *>(smem) + front;
+    KnnWarpScratch *scratch = reinterpret_cast<KnnWarpScratch *>(smem + (size_t)total * sizeof(float));
 
     const int lib = blockIdx.y;
-    const float *src = Y + (lib0 + lib) * ldY;
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        x[t] = src[t];
+    stage_series(reinterpret_cast<float *>(smem), Y + (lib0 + lib) * ldY, T, front, total);
     __syncthreads();
 
     const int warp = warp_id();
@@ -273,13 +292,14 @@ template <int J>
 static cudaError_t simplex_J(const float *Y, int64_t N, int T, int64_t ldY, int E_max, int tau, int Tp, int32_t *optE,
                              float *rho_by_E, cudaStream_t st)
 {
-    size_t smem = knn_smem_bytes(T, kKnnWarps);
+    const int front = front_pad(E_max, tau);
+    size_t smem = knn_smem_bytes_exact(T, front, J);
     cudaError_t e = cudaFuncSetAttribute(simplex_kernel<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     for (int64_t b = 0; b < N; b += 0x7fffffff) {
         int64_t n = N - b < 0x7fffffff ? N - b : 0x7fffffff;
-        simplex_kernel<J><<<(unsigned)n, kKnnThreads, smem, st>>>(Y + b * ldY, ldY, T, E_max, tau, Tp, optE + b,
+        simplex_kernel<J><<<(unsigned)n, kKnnThreads, smem, st>>>(Y + b * ldY, ldY, T, E_max, tau, Tp, front, optE + b,
                                                                    rho_by_E ? rho_by_E + b * E_max : nullptr);
     }
     return cudaGetLastError();
@@ -302,15 +322,17 @@ static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, i
                          uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw, int pE,
                          cudaStream_t st)
 {
-    size_t smem = knn_smem_bytes(T, kKnnWarps);
+    const int E_hi = 32 - __builtin_clz(sel);
+    const int front = front_pad(E_hi, tau);
+    size_t smem = knn_smem_bytes_exact(T, front, J);
     cudaError_t e =
         cudaFuncSetAttribute(knn_tables_kernel<J, kPublic>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     const int q_per_cta = 64;
     dim3 grid((unsigned)((T - Tp + q_per_cta - 1) / q_per_cta), (unsigned)n_lib);
-    knn_tables_kernel<J, kPublic><<<grid, kKnnThreads, smem, st>>>(Y, ldY, lib0, T, tau, Tp, excl, sel, q_per_cta, lay,
-                                                                    tables, pidx, pw, pE);
+    knn_tables_kernel<J, kPublic><<<grid, kKnnThreads, smem, st>>>(Y, ldY, lib0, T, tau, Tp, excl, sel, q_per_cta,
+                                                                    front, lay, tables, pidx, pw, pE);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,7 @@ struct LookupArgs {
 };
 
 size_t lookup_smem_bytes(int T);
-cudaError_t launch_lookup(const LookupArgs &a, cudaStream_t st);
+// All tiles in [tile_begin, tile_begin + n_tiles) must have this E.
+cudaError_t launch_lookup(const LookupArgs &a, int E, cudaStream_t st);
 
 }  // namespace edm

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) prep_targets_kernel(const float *__restri
 // ---------------------------------------------------------------------------
 // Lookup + rho.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kLkThreads, 1) lookup_kernel(LookupArgs a)
+__global__ void __launch_bounds__(kLkThreads, 1) lookup_generic_kernel(LookupArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
@@ -194,6 +194,129 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_kernel(LookupArgs a)
     }
 }
 
+// Fast path for k = E+1 <= kFastK: the row's k neighbour offsets and
+// weights live in registers, loaded one t-block ahead so the L2 latency of
+// the table overlaps the previous block's gathers; the neighbour loop is
+// unrolled so each step r issues k independent gathers.
+constexpr int kFastK = 12;
+
+template <int K>
+__global__ void __launch_bounds__(kLkThreads, 1) lookup_k_kernel(LookupArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t pad = (128u - (raw & 127u)) & 127u;
+    unsigned char *smem = smem_raw + pad;
+    float *tile_s = reinterpret_cast<float *>(smem);
+    float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * 32 * sizeof(float));
+    const uint32_t base = raw + pad;
+
+    const int tile = a.tile_begin + blockIdx.x;
+    const TileMeta m = a.meta[tile];
+    const int E = K - 1;
+    const int L = (E - 1) * a.tau;
+    const int Tq = a.T - a.Tp - L;
+    const int nblk = (Tq + 31) / 32;
+
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.tiles + (size_t)tile * a.T * 32);
+        float4 *dst = reinterpret_cast<float4 *>(tile_s);
+        const int n4 = a.T * 8;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x)
+            dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+
+    const int lane = lane_id(), warp = warp_id();
+    float *red = red_all + warp * 32 * kRedStride;
+    const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
+    const int lib_lo = blockIdx.y * per;
+    const int lib_hi = min(a.n_lib, lib_lo + per);
+    const uint32_t lane4 = (uint32_t)lane * 4u;
+    const size_t tq_pad = (size_t)a.lay.Tq_pad;
+
+    for (int lib = lib_lo + warp; lib < lib_hi; lib += kLkWarps) {
+        const uint8_t *lb = a.tables + (size_t)lib * a.lay.lib_stride;
+        const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
+        const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        float Sp[32], Spp[32], Spo[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            Sp[r] = 0.f;
+            Spp[r] = 0.f;
+            Spo[r] = 0.f;
+        }
+        float wq[K];
+        uint32_t iq[K];
+        {
+            const bool v = lane < Tq;
+#pragma unroll
+            for (int n = 0; n < K; ++n) {
+                wq[n] = v ? __ldg(Wt + n * tq_pad + lane) : 0.f;
+                iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane) : 0u;
+            }
+        }
+        for (int b = 0; b < nblk; ++b) {
+            const int row = b * 32 + lane;
+            const bool valid = row < Tq;
+            float wn[K];
+            uint32_t An[K];
+#pragma unroll
+            for (int n = 0; n < K; ++n) {
+                wn[n] = wq[n];
+                An[n] = base + iq[n] * 128u + lane4;
+            }
+            {  // prefetch the next block's entries
+                const int nrow = row + 32;
+                const bool v = nrow < Tq;
+#pragma unroll
+                for (int n = 0; n < K; ++n) {
+                    wq[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
+                    iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
+                }
+            }
+            const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
+            const uint32_t Ao = base + orow * 128u + lane4;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t x = (uint32_t)(r * 4);
+                float p = 0.f;
+#pragma unroll
+                for (int n = 0; n < K; ++n)
+                    p = fmaf(wn[n], lds_f32(An[n] ^ x), p);
+                const float o = lds_f32(Ao ^ x);
+                Sp[r] += p;
+                Spp[r] = fmaf(p, p, Spp[r]);
+                Spo[r] = fmaf(p, o, Spo[r]);
+            }
+        }
+        float tot[3];
+#pragma unroll
+        for (int mm = 0; mm < 3; ++mm) {
+            const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                red[r * kRedStride + lane] = S[r];
+            __syncwarp();
+            float sacc = 0.f;
+#pragma unroll
+            for (int l2 = 0; l2 < 32; ++l2)
+                sacc += red[(lane ^ l2) * kRedStride + l2];
+            tot[mm] = sacc;
+            __syncwarp();
+        }
+        if (lane < m.count) {
+            const int64_t j = a.pi[m.first + lane];
+            const float2 om = a.omom[m.first + lane];
+            const float n = (float)Tq;
+            const float num = n * tot[2] - tot[0] * om.x;
+            const float den_p = n * tot[1] - tot[0] * tot[0];
+            const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;
+            a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho;
+        }
+    }
+}
+
 cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
                                 const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st)
 {
@@ -203,17 +326,39 @@ cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_lookup(const LookupArgs &a, cudaStream_t st)
+template <class Kern>
+static cudaError_t launch_one(Kern kern, const LookupArgs &a, cudaStream_t st)
 {
-    if (a.n_tiles <= 0 || a.n_lib <= 0)
-        return cudaSuccess;
     size_t smem = lookup_smem_bytes(a.T);
-    cudaError_t e = cudaFuncSetAttribute(lookup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
-    lookup_kernel<<<grid, kLkThreads, smem, st>>>(a);
+    kern<<<grid, kLkThreads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+int lookup_fast_k() { return kFastK; }
+
+// All tiles of `a` must share one E (the caller splits blocks into runs).
+cudaError_t launch_lookup(const LookupArgs &a, int E, cudaStream_t st)
+{
+    if (a.n_tiles <= 0 || a.n_lib <= 0)
+        return cudaSuccess;
+    switch (E + 1) {
+    case 2: return launch_one(lookup_k_kernel<2>, a, st);
+    case 3: return launch_one(lookup_k_kernel<3>, a, st);
+    case 4: return launch_one(lookup_k_kernel<4>, a, st);
+    case 5: return launch_one(lookup_k_kernel<5>, a, st);
+    case 6: return launch_one(lookup_k_kernel<6>, a, st);
+    case 7: return launch_one(lookup_k_kernel<7>, a, st);
+    case 8: return launch_one(lookup_k_kernel<8>, a, st);
+    case 9: return launch_one(lookup_k_kernel<9>, a, st);
+    case 10: return launch_one(lookup_k_kernel<10>, a, st);
+    case 11: return launch_one(lookup_k_kernel<11>, a, st);
+    case 12: return launch_one(lookup_k_kernel<12>, a, st);
+    default: return launch_one(lookup_generic_kernel, a, st);
+    }
 }
 
 }  // namespace edm

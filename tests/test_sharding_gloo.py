@@ -1,0 +1,70 @@
+"""Multi-rank path on CPU: two gloo ranks shard phase 1 by series and phase 2
+by library rows, exchange optE once, and together reproduce the
+single-process result exactly (the compute steps here are the oracle)."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import edm_synth as synth
+from paper_2011_11082_gb300.sharding import run_sharded, shard_range
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, Y, E_max, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import oracle as orc
+
+    def opt(Ys):
+        return orc.optimal_E(Ys, E_max, nthreads=1)[0]
+
+    def rows(Yf, optE, b, e):
+        return orc.ccm_rho_rows(Yf, optE.numpy(), rows=np.arange(b, e), nthreads=1)
+
+    optE, (b, e), R = run_sharded(Y, opt, rows, world, rank)
+    np.save(os.path.join(out_dir, f"rows_{rank}.npy"), R)
+    np.save(os.path.join(out_dir, f"optE_{rank}.npy"), optE.numpy())
+    np.save(os.path.join(out_dir, f"range_{rank}.npy"), np.array([b, e]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shard_range_covers_exactly():
+    for n in (1, 7, 64, 101):
+        for w in (1, 2, 3, 8):
+            seen = []
+            for r in range(w):
+                b, e = shard_range(n, w, r)
+                seen.extend(range(b, e))
+            assert seen == list(range(n))
+
+
+def test_two_ranks_match_single_process(tmp_path):
+    from oracle import oracle as orc
+
+    Y = synth.coupled_logistic(13, 160, 0.1, 0.05, seed_data=21, seed_noise=22)
+    E_max = 5
+    port = _free_port()
+    mp.start_processes(_worker, args=(2, port, Y, E_max, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    oE, _ = orc.optimal_E(Y, E_max)
+    R = orc.ccm_rho_rows(Y, oE)
+    for r in range(2):
+        assert np.array_equal(np.load(tmp_path / f"optE_{r}.npy"), oE)
+    parts = [np.load(tmp_path / f"rows_{r}.npy") for r in range(2)]
+    ranges = [tuple(np.load(tmp_path / f"range_{r}.npy")) for r in range(2)]
+    assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and ranges[1][1] == 13
+    assert np.array_equal(np.concatenate(parts), R)
