@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 WORKLOADS = {
     # name: (N, T, density, b_max, E_max)
     "n101729_t1500": (101729, 1500, 0.0001, 0.02, 20),
-    "n16384_t1500": (16384, 1500, 0.01, 0.02, 20),
+    "n16384_t1500": (16384, 1500, 0.001, 0.02, 20),
     "n2048_t1500": (2048, 1500, 0.01, 0.02, 20),
     "n64_t500": (64, 500, 0.05, 0.05, 10),
 }
@@ -168,6 +168,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n101729_t1500", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--lookup", default="chunked", choices=["chunked", "scalar"],
+                    help="phase-2 gather kernels: 16-byte chunked (default) or scalar (comparison)")
     ap.add_argument("--cpu-rows", type=int, default=0, help="library rows the oracle times (0: 2 x cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -200,13 +202,14 @@ def main():
     Y = edm_synth.coupled_logistic(N, T, dens, bmax, seed_data=rank, seed_noise=1 + rank)
     Yd = torch.from_numpy(Y).to(dev)
     prec = edm.EDM_PRECISION_FP16_TARGETS if args.precision == "fp16" else edm.EDM_PRECISION_FP32
+    flags = edm.EDM_FLAG_LOOKUP_SCALAR if args.lookup == "scalar" else 0
     rho = torch.empty((N, N), dtype=torch.float32, device=dev)
     ws = torch.empty(edm.edm_ccm_workspace_bytes(N, T, precision=prec), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
         optE, _ = edm.edm_optimal_E(Yd, E_max=E_max, return_rho=False)
-        edm.edm_ccm_rho(Yd, optE, precision=prec, out=rho, workspace=ws)
+        edm.edm_ccm_rho(Yd, optE, precision=prec, out=rho, workspace=ws, flags=flags)
         return optE
 
     for _ in range(args.warmup):
@@ -239,7 +242,7 @@ def main():
     for k in range(4):
         m, n, u = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
         lib.edm_profile_read(k, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
-        prof[_abi.KERNEL_NAMES[k]] = {"ms": m.value / args.steps, "launches": n.value // args.steps,
+        prof[_abi.KERNEL_NAMES[k]] = {"ms": m.value / args.steps, "launches": n.value / args.steps,
                                       "units": u.value / args.steps}
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -302,7 +305,7 @@ def main():
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16-targets/f32-accumulate",
             "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "T": T, "E_max": E_max, "tau": 1, "Tp": 1,
-                       "precision": args.precision, "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)",
+                       "precision": args.precision, "lookup": args.lookup, "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)",
                        "optE_histogram": hist},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "kernels": prof,

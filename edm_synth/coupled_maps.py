@@ -50,7 +50,9 @@ class WorkloadSpec:
 WORKLOADS = {
     "n64_t500": WorkloadSpec("n64_t500", 64, 500, 0.05, 0.05, 10),
     "n2048_t1500": WorkloadSpec("n2048_t1500", 2048, 1500, 0.01, 0.02, 20),
-    "n16384_t1500": WorkloadSpec("n16384_t1500", 16384, 1500, 0.01, 0.02, 20),
+    # 1% density at N=16,384 would give each map ~164 inputs and drive it out
+    # of (0,1); 0.1% keeps ~16 inputs per map, as in the N=2,048 workload.
+    "n16384_t1500": WorkloadSpec("n16384_t1500", 16384, 1500, 0.001, 0.02, 20),
     "n101729_t1500": WorkloadSpec("n101729_t1500", 101729, 1500, 0.0001, 0.02, 20),
 }
 

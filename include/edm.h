@@ -46,10 +46,14 @@ extern "C" {
 #define EDM_MAX_T 65535
 
 #define EDM_PRECISION_FP32 0         /* targets staged as float32 */
-#define EDM_PRECISION_FP16_TARGETS 1 /* targets staged as float16, FP32 accumulation */
+#define EDM_PRECISION_FP16_TARGETS 1 /* targets staged as float16 (for E <= 11; larger
+                                        E stay float32), FP32 accumulation */
 
 /* flags */
 #define EDM_FLAG_NONE 0u
+/* phase 2: use the scalar-gather lookup kernels instead of the 16-byte
+   chunked ones (FP32 targets only; kept for comparison) */
+#define EDM_FLAG_LOOKUP_SCALAR 1u
 
 typedef struct edm_params {
     int32_t E_max;            /* phase 1 searches E = 1..E_max (<= EDM_MAX_E) */

@@ -18,6 +18,7 @@ from ._abi import (
     EDM_MAX_E,
     EDM_PRECISION_FP16_TARGETS,
     EDM_PRECISION_FP32,
+    EDM_FLAG_LOOKUP_SCALAR,
     EdmError,
     edm_params,
 )
@@ -98,7 +99,8 @@ def edm_ccm_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion
 
 def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_count: int | None = None,
                 tau: int = 1, Tp: int = 1, exclusion_radius: int = 0, precision: int = EDM_PRECISION_FP32,
-                out: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                out: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None,
+                flags: int = 0) -> torch.Tensor:
     """Phase 2 cross map for libraries [lib_begin, lib_begin+lib_count).
 
     Returns the TARGET-MAJOR block ``out[j][i - lib_begin] = rho(library i ->
@@ -115,7 +117,7 @@ def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_cou
     if not (out.is_cuda and out.dtype == torch.float32 and out.dim() == 2 and out.stride(1) == 1
             and out.shape[0] == N and out.shape[1] >= lib_count):
         raise TypeError("out must be a float32 CUDA tensor [N][>=lib_count] with unit inner stride")
-    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision, flags=flags)
     need = int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)

@@ -18,6 +18,7 @@ EDM_MAX_E = 20
 EDM_MAX_T = 65535
 EDM_PRECISION_FP32 = 0
 EDM_PRECISION_FP16_TARGETS = 1
+EDM_FLAG_LOOKUP_SCALAR = 1
 
 
 class edm_params(ctypes.Structure):

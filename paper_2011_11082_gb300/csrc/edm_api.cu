@@ -276,9 +276,11 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
         return EDM_ERR_INVALID;
     if (T > EDM_MAX_T || N > 0x7fffffffLL)
         return EDM_ERR_UNSUPPORTED;
-    if (params->precision != EDM_PRECISION_FP32)
-        return EDM_ERR_UNSUPPORTED;
-    if (T > edm::knn_max_T() || edm::lookup_smem_bytes((int)T) > 227u * 1024u)
+    const bool scalar = (params->flags & EDM_FLAG_LOOKUP_SCALAR) != 0;
+    if (scalar && params->precision != EDM_PRECISION_FP32)
+        return EDM_ERR_INVALID;
+    if (T > edm::knn_max_T() ||
+        (scalar ? edm::lookup_smem_bytes((int)T) : edm::chunked_smem_bytes((int)T)) > 227u * 1024u)
         return EDM_ERR_UNSUPPORTED;
     const CcmWs L = ccm_ws_layout(N, T, params);
     if (ws_bytes < L.total)
@@ -309,9 +311,14 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
             pi[(size_t)fill[E_host[(size_t)j]]++] = (int32_t)j;
     }
     std::vector<edm::TileMeta> tiles;
-    for (int E = 1; E <= EDM_MAX_E; ++E)
-        for (int64_t c = 0; c < count[E]; c += 32)
-            tiles.push_back(edm::TileMeta{E, (int)(start[E] + c), (int)std::min<int64_t>(32, count[E] - c), 0});
+    const bool want_f16 = params->precision == EDM_PRECISION_FP16_TARGETS;
+    for (int E = 1; E <= EDM_MAX_E; ++E) {
+        const bool f16 = want_f16 && E + 1 <= edm::kF16MaxK;
+        const int width = f16 ? 64 : 32;
+        for (int64_t c = 0; c < count[E]; c += width)
+            tiles.push_back(edm::TileMeta{E, (int)(start[E] + c), (int)std::min<int64_t>(width, count[E] - c),
+                                          f16 ? edm::kTileF16 : 0});
+    }
     const int n_tiles = (int)tiles.size();
 
     unsigned char *wsb = (unsigned char *)ws;
@@ -326,6 +333,9 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
         LaunchScope ls(EDM_KERNEL_PREP, st, (double)N);
         EDM_CUDA(edm::launch_prep_targets(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles, tiles_d,
                                           omom_d, st));
+        if (want_f16)
+            EDM_CUDA(edm::launch_prep_targets_f16(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles,
+                                                  (uint8_t *)tiles_d, omom_d, st));
     }
 
     // --- target blocks (L2-sized) x library blocks ------------------------------
@@ -349,6 +359,7 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
             // one launch per run of equal E inside the target block
             for (int r0 = tb0; r0 < tb0 + ntb;) {
                 const int E = tiles[(size_t)r0].E;
+                const bool f16 = (tiles[(size_t)r0].flags & edm::kTileF16) != 0;
                 int r1 = r0;
                 int64_t targets = 0;
                 while (r1 < tb0 + ntb && tiles[(size_t)r1].E == E)
@@ -374,7 +385,10 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
                 a.ld_rho = ld_rho;
                 {
                     LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                    EDM_CUDA(edm::launch_lookup(a, E, st));
+                    if (scalar)
+                        EDM_CUDA(edm::launch_lookup(a, E, st));
+                    else
+                        EDM_CUDA(edm::launch_lookup_chunked(a, E, f16, st));
                 }
                 r0 = r1;
             }

@@ -35,12 +35,17 @@ cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_l
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
                               int32_t *idx, float *w, cudaStream_t st);
 
-// Target tiles: 32 targets of one E, time-major [T][32] float (z-normalised).
+// Target tiles: one E each, time-major rows of 128 bytes (z-normalised):
+// FP32 tiles hold 32 targets ([T][32] float); FP16 tiles (flag kTileF16)
+// hold 64 ([T][32] half2, word w = targets w and w+32).
+constexpr int kTileF16 = 1;
+// FP16 tiles are used for E + 1 <= kF16MaxK; larger E stay FP32.
+constexpr int kF16MaxK = 12;
 struct TileMeta {
     int E;
     int first;  // first sorted position
-    int count;  // targets in this tile (<= 32)
-    int pad;
+    int count;  // targets in this tile (<= 32, or <= 64 for FP16)
+    int flags;  // kTileF16
 };
 
 cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
@@ -65,5 +70,10 @@ struct LookupArgs {
 size_t lookup_smem_bytes(int T);
 // All tiles in [tile_begin, tile_begin + n_tiles) must have this E.
 cudaError_t launch_lookup(const LookupArgs &a, int E, cudaStream_t st);
+// 16-byte chunked gathers (FP32 or FP16 tiles); same contract.
+size_t chunked_smem_bytes(int T);
+cudaError_t launch_lookup_chunked(const LookupArgs &a, int E, bool f16, cudaStream_t st);
+cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
+                                    const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st);
 
 }  // namespace edm

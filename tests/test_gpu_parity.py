@@ -166,3 +166,41 @@ def test_ccm_deterministic(edm):
     a = edm.edm_ccm_rho(Yd, optE).cpu().numpy()
     b = edm.edm_ccm_rho(Yd, optE).cpu().numpy()
     assert np.array_equal(a, b, equal_nan=True)
+
+
+# ---------------------------------------------------------------------------
+# FP16-target form: rho error against the FP64 oracle within 1e-3; and the
+# scalar-gather kernels (comparison path) at the FP32 bar.
+FP16_TOL = 1e-3
+
+
+def test_ccm_fp16_targets_small_workload(edm):
+    Y = synth.workload("n64_t500")
+    oE, _ = orc.optimal_E(Y, 10)
+    rho_t = edm.edm_ccm_rho(_dev(Y), torch.from_numpy(oE).cuda(), precision=edm.EDM_PRECISION_FP16_TARGETS)
+    R = orc.ccm_rho_rows(Y, oE)
+    assert np.abs(rho_t.t().cpu().numpy() - R).max() < FP16_TOL
+
+
+def test_ccm_fp16_targets_n2048_rows_and_large_E(edm):
+    Y = synth.workload("n2048_t1500")
+    Yd = _dev(Y)
+    optE, _ = edm.edm_optimal_E(Yd, E_max=20)
+    oE = optE.cpu().numpy()
+    assert oE.max() >= 12  # exercises the FP32 fallback tiles of large E too
+    rho_t = edm.edm_ccm_rho(Yd, optE, precision=edm.EDM_PRECISION_FP16_TARGETS)
+    rows = np.random.default_rng(4).choice(Y.shape[0], 8, replace=False)
+    R = orc.ccm_rho_rows(Y, oE, rows=rows)
+    err = np.abs(rho_t.cpu().numpy()[:, rows].T - R)
+    assert err.max() < FP16_TOL, err.max()
+
+
+def test_ccm_scalar_lookup_matches(edm):
+    Y = synth.coupled_logistic(90, 400, 0.05, 0.05, seed_data=19, seed_noise=20)
+    oE = np.random.default_rng(6).integers(1, 16, size=90).astype(np.int32)
+    R = orc.ccm_rho_rows(Y, oE)
+    Yd, Ed = _dev(Y), torch.from_numpy(oE).cuda()
+    got = edm.edm_ccm_rho(Yd, Ed, flags=edm.EDM_FLAG_LOOKUP_SCALAR).t().cpu().numpy()
+    assert np.abs(got - R).max() < RHO_TOL
+    got2 = edm.edm_ccm_rho(Yd, Ed).t().cpu().numpy()
+    assert np.abs(got2 - R).max() < RHO_TOL
