@@ -120,6 +120,27 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
 /* Workspace edm_ccm_rho needs for N series of length T (bytes). */
 size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
 
+/*
+ * Adjoint of the cross map (not in the paper): given G = dL/d rho,
+ * grad_Y = dL/dY for L = sum_ij G(i,j) rho(i,j), with every kNN index and
+ * every optE held at the values the forward pass finds (the tables are
+ * rebuilt exactly).  Through the target y_j: the prediction p(t) and the
+ * observation y_j(t+Tp); through the library x_i: the weights
+ * exp(-d/d_1)/sum and d = sqrt(sum of squared lag differences).  Where a
+ * distance is 0 the gradient through it is 0.
+ *   grad_rho  TARGET-MAJOR like rho: grad_rho[j*ld_g + i] = dL/d rho(i,j),
+ *             ld_g >= N
+ *   grad_Y    [N][ldY] float32, overwritten
+ *   ws        at least edm_ccm_backward_workspace_bytes(N, T, params)
+ * Requires T - Tp <= 3072.  Synchronises `stream` once (reads optE).
+ * Summation order of the shared-memory accumulations varies between runs
+ * (atomic adds), so the last bits of grad_Y may differ run to run.
+ */
+int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                         const float *grad_rho, int64_t ld_g, const edm_params *params, float *grad_Y,
+                         void *ws, size_t ws_bytes, void *stream);
+size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
+
 /* Human-readable text for a status code (includes the CUDA error if any). */
 const char *edm_status_string(int status);
 

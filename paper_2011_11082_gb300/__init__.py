@@ -28,7 +28,11 @@ __all__ = [
     "edm_knn_table",
     "edm_ccm_rho",
     "edm_ccm_workspace_bytes",
+    "edm_ccm_rho_backward",
+    "edm_ccm_backward_workspace_bytes",
     "ccm",
+    "ccm_rho_autograd",
+    "CCMRhoFunction",
     "make_params",
     "EdmError",
     "EDM_MAX_E",
@@ -125,6 +129,65 @@ def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_cou
                          out.data_ptr(), _ld(out), workspace.data_ptr(), workspace.numel(), _stream(stream))
     _abi.check(st, "edm_ccm_rho")
     return out
+
+
+def edm_ccm_backward_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0) -> int:
+    lib = _abi.load()
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius)
+    return int(lib.edm_ccm_backward_workspace_bytes(N, T, ctypes.byref(p)))
+
+
+def edm_ccm_rho_backward(Y: torch.Tensor, optE: torch.Tensor, grad_rho_t: torch.Tensor, tau: int = 1, Tp: int = 1,
+                         exclusion_radius: int = 0, workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dL/dY for L = sum_ij G(i,j) rho(i,j), indices and optE frozen.
+
+    ``grad_rho_t`` is TARGET-MAJOR like the forward output:
+    grad_rho_t[j][i] = dL/d rho(library i -> target j)."""
+    lib = _abi.load()
+    Y = _dev_f32(Y, "Y")
+    N, T = Y.shape
+    if not (optE.is_cuda and optE.dtype == torch.int32 and optE.numel() == N and optE.is_contiguous()):
+        raise TypeError("optE must be a contiguous int32 CUDA tensor of N entries")
+    g = _dev_f32(grad_rho_t, "grad_rho_t")
+    if g.shape[0] != N or g.shape[1] < N:
+        raise TypeError("grad_rho_t must be [N][>=N]")
+    grad = torch.empty_like(Y)
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius)
+    need = int(lib.edm_ccm_backward_workspace_bytes(N, T, ctypes.byref(p)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)
+    st = lib.edm_ccm_rho_backward(Y.data_ptr(), N, T, _ld(Y), optE.data_ptr(), g.data_ptr(), _ld(g), ctypes.byref(p),
+                                  grad.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _abi.check(st, "edm_ccm_rho_backward")
+    return grad
+
+
+class CCMRhoFunction(torch.autograd.Function):
+    """rho(library i -> target j) as a differentiable function of the series
+    (library-major N x N output); optE and the neighbour indices are held
+    fixed, as in the adjoint entry point."""
+
+    @staticmethod
+    def forward(ctx, Y, optE, tau=1, Tp=1, exclusion_radius=0, precision=EDM_PRECISION_FP32):
+        Yc = Y.contiguous()
+        rho_t = edm_ccm_rho(Yc, optE, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+        ctx.save_for_backward(Yc, optE)
+        ctx.cfg = (tau, Tp, exclusion_radius)
+        return rho_t.t()
+
+    @staticmethod
+    def backward(ctx, g):
+        Y, optE = ctx.saved_tensors
+        tau, Tp, excl = ctx.cfg
+        grad = edm_ccm_rho_backward(Y, optE, g.t().contiguous(), tau=tau, Tp=Tp, exclusion_radius=excl)
+        return grad, None, None, None, None, None
+
+
+def ccm_rho_autograd(Y: torch.Tensor, optE: torch.Tensor, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,
+                     precision: int = EDM_PRECISION_FP32) -> torch.Tensor:
+    """Library-major rho [N][N] with autograd support (backward through the
+    hand-written adjoint kernels)."""
+    return CCMRhoFunction.apply(Y, optE, tau, Tp, exclusion_radius, precision)
 
 
 def ccm(Y: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,

@@ -1,0 +1,277 @@
+// backward.cu -- adjoint of the cross map: dL/dY for L = sum_ij g_ij rho_ij
+// with every kNN index and every optimal E held fixed.
+//
+// The paper has no gradients; this differentiates its rho (simplex weights
+// w = exp(-d/d_1)/sum, Algorithm 5 lookup, Pearson corrcoef).  For one pair
+// (library x, target y, rows t of the table):
+//   p_t = sum_n w_tn y(s_tn + Tp),  o_t = y(t + Tp),
+//   d rho / d p_t = a_t = alpha (o_t - o_bar) - beta (p_t - p_bar),
+//   d rho / d o_t = b_t = alpha (p_t - p_bar) - gamma (o_t - o_bar),
+//   alpha = g / sqrt(Vp Vo), beta = g rho / Vp, gamma = g rho / Vo
+// (g = dL/d rho folded in).  Target side: y(s_tn + Tp) += a_t w_tn,
+// y(t + Tp) += b_t.  Library side, through the weights:
+//   H_tn = sum_targets a_t (y(s_tn + Tp) - p_t),
+//   dL/dd_tn = -(w_tn / d_t1) H_tn (n >= 2),
+//   dL/dd_t1 = sum_{n>=2} (w_tn d_tn / d_t1^2) H_tn,
+// then d_tn = sqrt(sum_m (x(t - m tau) - x(s_tn - m tau))^2) carries it to x.
+// Where d = 0 (or d_t1 = 0, duplicate-only weights) the gradient is 0.
+//
+// Pass 1 (one CTA per target) also stores (alpha, beta, p_bar) per pair for
+// pass 2 (one CTA per library).  Both accumulate in shared memory with
+// atomic adds and then add their row of grad_Y once.
+#include "edm_internal.cuh"
+#include "launchers.h"
+
+namespace edm {
+
+constexpr int kBwThreads = 256;
+constexpr int kBwMaxRows = 12;  // rows per thread: T - Tp <= 12 * 256
+
+__device__ __forceinline__ double block_sum_d(double v, double *sh)
+{
+    v = warp_sum_d(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0)
+        sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum_d(t);
+        if (threadIdx.x == 0)
+            sh[0] = t;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+// Pass 1: one CTA per target j, libraries lib0 .. lib0+n_lib-1.
+__global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *y = reinterpret_cast<float *>(smem);
+    float *gy = y + a.T;
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    const float *src = a.Y + (int64_t)j * a.ldY;
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
+        y[t] = src[t];
+        gy[t] = 0.f;
+    }
+    __syncthreads();
+    const int E = a.optE[j], k = E + 1;
+    const int L = (E - 1) * a.tau;
+    const int Tq = a.T - a.Tp - L;
+    const double n = (double)Tq;
+    // observation window statistics (once per target)
+    double so = 0.0;
+    for (int r = threadIdx.x; r < Tq; r += blockDim.x)
+        so += (double)y[L + r + a.Tp];
+    so = block_sum_d(so, sh);
+    const double ob = so / n;
+    double vo = 0.0;
+    for (int r = threadIdx.x; r < Tq; r += blockDim.x) {
+        double d = (double)y[L + r + a.Tp] - ob;
+        vo += d * d;
+    }
+    vo = block_sum_d(vo, sh);
+    if (threadIdx.x == 0)
+        a.obar[j] = (float)ob;
+
+    for (int li = 0; li < a.n_lib; ++li) {
+        const int64_t i = a.lib0 + li;
+        const uint8_t *lb = a.tables + (size_t)li * a.lay.lib_stride;
+        const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
+        const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        const size_t tq = (size_t)a.lay.Tq_pad;
+        float p[kBwMaxRows];
+        double sp = 0.0;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q) {
+            const int r = threadIdx.x + q * kBwThreads;
+            p[q] = 0.f;
+            if (r < Tq) {
+                float acc = 0.f;
+                for (int nn = 0; nn < k; ++nn)
+                    acc = fmaf(Wt[nn * tq + r], y[It[nn * tq + r]], acc);
+                p[q] = acc;
+                sp += (double)acc;
+            }
+        }
+        sp = block_sum_d(sp, sh);
+        const double pb = sp / n;
+        double vp = 0.0, c = 0.0;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q) {
+            const int r = threadIdx.x + q * kBwThreads;
+            if (r < Tq) {
+                const double dp = (double)p[q] - pb;
+                vp += dp * dp;
+                c += dp * ((double)y[L + r + a.Tp] - ob);
+            }
+        }
+        vp = block_sum_d(vp, sh);
+        c = block_sum_d(c, sh);
+        const double g = (double)a.grad_rho[(int64_t)j * a.ld_g + i];
+        double alpha = 0.0, beta = 0.0, gam = 0.0;
+        if (vp > 0.0 && vo > 0.0) {
+            const double sq = sqrt(vp * vo);
+            const double rho = c / sq;
+            alpha = g / sq;
+            beta = g * rho / vp;
+            gam = g * rho / vo;
+        }
+        if (threadIdx.x == 0)
+            a.stats[i * a.N + j] = make_float4((float)alpha, (float)beta, (float)pb, 0.f);
+        const float fa = (float)alpha, fb = (float)beta, fg = (float)gam, fpb = (float)pb, fob = (float)ob;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q) {
+            const int r = threadIdx.x + q * kBwThreads;
+            if (r < Tq) {
+                const float ov = y[L + r + a.Tp] - fob, pv = p[q] - fpb;
+                const float at = fa * ov - fb * pv;
+                const float bt = fa * pv - fg * ov;
+                for (int nn = 0; nn < k; ++nn)
+                    atomicAdd(&gy[It[nn * tq + r]], at * Wt[nn * tq + r]);
+                atomicAdd(&gy[L + r + a.Tp], bt);
+            }
+        }
+        __syncthreads();
+    }
+    float *dst = a.grad_Y + (int64_t)j * a.ldY;
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+        dst[t] += gy[t];
+}
+
+// Pass 2: one CTA per library in the block.  H is [k][rows of the chunk].
+__global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_rows)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *x = reinterpret_cast<float *>(smem);
+    float *gx = x + a.T;
+    float *yb = gx + a.T;
+    float *H = yb + a.T;
+    const int li = blockIdx.x;
+    const int64_t i = a.lib0 + li;
+    const float *src = a.Y + i * a.ldY;
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
+        x[t] = src[t];
+        gx[t] = 0.f;
+    }
+    __syncthreads();
+    const uint8_t *lb = a.tables + (size_t)li * a.lay.lib_stride;
+    const size_t tq = (size_t)a.lay.Tq_pad;
+    for (int E = 1; E <= EDM_MAX_E; ++E) {
+        const int j0 = a.e_start[E], j1 = a.e_start[E + 1];
+        if (j0 == j1)
+            continue;
+        const int k = E + 1;
+        const int L = (E - 1) * a.tau;
+        const int Tq = a.T - a.Tp - L;
+        const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
+        const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        for (int r0 = 0; r0 < Tq; r0 += h_rows) {
+            const int rn = min(h_rows, Tq - r0);
+            for (int q = threadIdx.x; q < k * rn; q += blockDim.x)
+                H[q] = 0.f;
+            __syncthreads();
+            for (int pj = j0; pj < j1; ++pj) {
+                const int j = a.pi[pj];
+                const float *ys = a.Y + (int64_t)j * a.ldY;
+                for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+                    yb[t] = ys[t];
+                __syncthreads();
+                const float4 st = a.stats[i * a.N + j];
+                const float ob = a.obar[j];
+                for (int rr = threadIdx.x; rr < rn; rr += blockDim.x) {
+                    const int r = r0 + rr;
+                    float pv = 0.f;
+                    for (int nn = 0; nn < k; ++nn)
+                        pv = fmaf(Wt[nn * tq + r], yb[It[nn * tq + r]], pv);
+                    const float at = st.x * (yb[L + r + a.Tp] - ob) - st.y * (pv - st.z);
+                    for (int nn = 0; nn < k; ++nn)
+                        H[nn * rn + rr] += at * (yb[It[nn * tq + r]] - pv);
+                }
+                __syncthreads();
+            }
+            // chain H through the weights and distances into x
+            for (int rr = threadIdx.x; rr < rn; rr += blockDim.x) {
+                const int r = r0 + rr;
+                const int t = L + r;
+                float d[EDM_MAX_E + 1];
+                for (int nn = 0; nn < k; ++nn) {
+                    const int s = (int)It[nn * tq + r] - a.Tp;
+                    float acc = 0.f;
+                    for (int m = 0; m < E; ++m) {
+                        float df = x[t - m * a.tau] - x[s - m * a.tau];
+                        acc = fmaf(df, df, acc);
+                    }
+                    d[nn] = sqrtf(acc);
+                }
+                const float d1 = d[0];
+                if (!(d1 > 0.f))
+                    continue;  // duplicate-only weights: constant
+                float g0 = 0.f;
+                for (int nn = 1; nn < k; ++nn) {
+                    const float wv = Wt[nn * tq + r];
+                    const float h = H[nn * rn + rr];
+                    g0 += wv * d[nn] / (d1 * d1) * h;
+                    const float gn = -(wv / d1) * h;
+                    if (d[nn] > 0.f) {
+                        const int s = (int)It[nn * tq + r] - a.Tp;
+                        const float cf = gn / d[nn];
+                        for (int m = 0; m < E; ++m) {
+                            float df = x[t - m * a.tau] - x[s - m * a.tau];
+                            atomicAdd(&gx[t - m * a.tau], cf * df);
+                            atomicAdd(&gx[s - m * a.tau], -cf * df);
+                        }
+                    }
+                }
+                {
+                    const int s = (int)It[r] - a.Tp;
+                    const float cf = g0 / d1;
+                    for (int m = 0; m < E; ++m) {
+                        float df = x[t - m * a.tau] - x[s - m * a.tau];
+                        atomicAdd(&gx[t - m * a.tau], cf * df);
+                        atomicAdd(&gx[s - m * a.tau], -cf * df);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    float *dst = a.grad_Y + i * a.ldY;
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+        dst[t] += gx[t];
+}
+
+int bw_max_T() { return kBwMaxRows * kBwThreads; }
+
+static size_t bw_lib_smem(int T, int h_rows, int kmax) { return (size_t)3 * T * 4 + (size_t)h_rows * kmax * 4; }
+
+cudaError_t launch_backward(const BwArgs &a, int kmax, cudaStream_t st)
+{
+    size_t s1 = (size_t)2 * a.T * 4;
+    cudaError_t e = cudaFuncSetAttribute(bw_target_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+    if (e != cudaSuccess)
+        return e;
+    bw_target_kernel<<<a.N, kBwThreads, s1, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    // H chunk: as many rows as fit next to x, gx and the target buffer
+    const size_t budget = 200 * 1024 - (size_t)3 * a.T * 4;
+    int h_rows = (int)(budget / ((size_t)kmax * 4));
+    if (h_rows > a.T)
+        h_rows = a.T;
+    if (h_rows < 32)
+        return cudaErrorInvalidValue;
+    size_t s2 = bw_lib_smem(a.T, h_rows, kmax);
+    if ((e = cudaFuncSetAttribute(bw_library_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) !=
+        cudaSuccess)
+        return e;
+    bw_library_kernel<<<a.n_lib, kBwThreads, s2, st>>>(a, h_rows);
+    return cudaGetLastError();
+}
+
+}  // namespace edm

@@ -397,4 +397,119 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
     return EDM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kBwTableBytes = 256ull << 20;
+
+struct BwWs {
+    size_t pi, e_start, obar, stats, tables, table_bytes, total;
+};
+
+BwWs bw_layout(int64_t N, int64_t T, const edm_params *p)
+{
+    BwWs w;
+    size_t off = 0;
+    w.pi = off;
+    off += align256((size_t)N * 4);
+    w.e_start = off;
+    off += 256;
+    w.obar = off;
+    off += align256((size_t)N * 4);
+    w.stats = off;
+    off += align256((size_t)N * (size_t)N * 16);
+    w.tables = off;
+    edm::TableLayout all = make_layout((1u << EDM_MAX_E) - 1u, T, p);
+    w.table_bytes = std::max(kBwTableBytes, (size_t)all.lib_stride);
+    off += align256(w.table_bytes);
+    w.total = off;
+    return w;
+}
+}  // namespace
+
+size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *params)
+{
+    if (!params || N < 1 || T < 2)
+        return 0;
+    return bw_layout(N, T, params).total;
+}
+
+int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                         const float *grad_rho, int64_t ld_g, const edm_params *params, float *grad_Y, void *ws,
+                         size_t ws_bytes, void *stream)
+{
+    int rc = check_common(params);
+    if (rc)
+        return rc;
+    if (!Y || !optE || !grad_rho || !grad_Y || !ws || N < 1 || T < 2 || ldY < T || ld_g < N)
+        return EDM_ERR_INVALID;
+    if (T > EDM_MAX_T || N > 0x7fffffffLL || T - params->Tp > edm::bw_max_T() || T > edm::knn_max_T())
+        return EDM_ERR_UNSUPPORTED;
+    const BwWs L = bw_layout(N, T, params);
+    if (ws_bytes < L.total)
+        return EDM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> E_host((size_t)N);
+    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaStreamSynchronize(st));
+    int32_t start[EDM_MAX_E + 2] = {0};
+    int64_t count[EDM_MAX_E + 2] = {0};
+    uint32_t sel = 0;
+    int kmax = 2;
+    for (int64_t j = 0; j < N; ++j) {
+        int E = E_host[(size_t)j];
+        if (E < 1 || E > EDM_MAX_E || ccm_min_candidates(T, E, params) < E + 1)
+            return EDM_ERR_INVALID;
+        count[E]++;
+        sel |= 1u << (E - 1);
+        kmax = std::max(kmax, E + 1);
+    }
+    for (int E = 1; E <= EDM_MAX_E; ++E)
+        start[E + 1] = start[E] + (int32_t)count[E];
+    std::vector<int32_t> pi((size_t)N);
+    {
+        int32_t fill[EDM_MAX_E + 2];
+        memcpy(fill, start, sizeof fill);
+        for (int64_t j = 0; j < N; ++j)
+            pi[(size_t)fill[E_host[(size_t)j]]++] = (int32_t)j;
+    }
+    unsigned char *wsb = (unsigned char *)ws;
+    EDM_CUDA(cudaMemcpyAsync(wsb + L.pi, pi.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+    EDM_CUDA(cudaMemcpyAsync(wsb + L.e_start, start, sizeof start, cudaMemcpyHostToDevice, st));
+    EDM_CUDA(cudaMemset2DAsync(grad_Y, (size_t)ldY * 4, 0, (size_t)T * 4, (size_t)N, st));
+    const edm::TableLayout lay = make_layout(sel, T, params);
+    const int64_t per_block =
+        std::min<int64_t>(65535, std::max<int64_t>(1, (int64_t)(L.table_bytes / (size_t)lay.lib_stride)));
+    for (int64_t lb0 = 0; lb0 < N; lb0 += per_block) {
+        const int nlb = (int)std::min<int64_t>(per_block, N - lb0);
+        {
+            LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel));
+            EDM_CUDA(edm::launch_knn_tables(Y, ldY, lb0, nlb, (int)T, params->tau, params->Tp,
+                                            params->exclusion_radius, sel, lay, wsb + L.tables, st));
+        }
+        edm::BwArgs a;
+        a.Y = Y;
+        a.ldY = ldY;
+        a.T = (int)T;
+        a.tau = params->tau;
+        a.Tp = params->Tp;
+        a.optE = optE;
+        a.grad_rho = grad_rho;
+        a.ld_g = ld_g;
+        a.tables = wsb + L.tables;
+        a.lay = lay;
+        a.lib0 = lb0;
+        a.n_lib = nlb;
+        a.N = (int)N;
+        a.stats = (float4 *)(wsb + L.stats);
+        a.obar = (float *)(wsb + L.obar);
+        a.pi = (const int32_t *)(wsb + L.pi);
+        a.e_start = (const int32_t *)(wsb + L.e_start);
+        a.grad_Y = grad_Y;
+        EDM_CUDA(edm::launch_backward(a, kmax, st));
+    }
+    return EDM_OK;
+}
+
 }  // extern "C"

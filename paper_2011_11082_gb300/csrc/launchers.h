@@ -76,4 +76,26 @@ cudaError_t launch_lookup_chunked(const LookupArgs &a, int E, bool f16, cudaStre
 cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
                                     const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st);
 
+// Adjoint (backward.cu).
+struct BwArgs {
+    const float *Y;
+    int64_t ldY;
+    int T, tau, Tp;
+    const int32_t *optE;
+    const float *grad_rho;
+    int64_t ld_g;
+    const uint8_t *tables;
+    TableLayout lay;
+    int64_t lib0;
+    int n_lib;
+    int N;
+    float4 *stats;
+    float *obar;
+    const int32_t *pi;
+    const int32_t *e_start;
+    float *grad_Y;
+};
+int bw_max_T();
+cudaError_t launch_backward(const BwArgs &a, int kmax, cudaStream_t st);
+
 }  // namespace edm
