@@ -141,6 +141,35 @@ int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, cons
                          void *ws, size_t ws_bytes, void *stream);
 size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
 
+/*
+ * Allocation-free variant of edm_ccm_rho, for callers that cannot allocate
+ * device memory while they run (code inside a stream capture, where
+ * cudaMalloc is not allowed; real-time loops that must not touch an
+ * allocator; hosts that hand this library a stream but no memory pool).
+ * The paper has no counterpart: this is a deployment form of the same
+ * cross map.  Inputs, outputs and results are those of edm_ccm_rho; the
+ * scratch lives in one statically allocated 64 MiB device array instead of
+ * a caller workspace, and the plan is built on the device, so the call
+ * makes no cudaMalloc/cudaFree, no allocating library call and no host heap
+ * allocation.
+ *   - Problems whose scratch exceeds the array (target tiles of about
+ *     N*T*4 bytes plus the kNN tables of at least one library) return
+ *     EDM_ERR_WORKSPACE before touching the device; e.g. N = 2,048 and
+ *     T = 1,500 fit, N = 16,384 and T = 1,500 do not.
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress, that device current); make that first call
+ *     before any stream capture.
+ *   - Every GPU that loads the library holds the array until the process
+ *     exits.  All calls share it and it keeps the previous call's contents;
+ *     calls whose GPU work overlaps (other streams, other host threads)
+ *     race on it.
+ *   - Like edm_ccm_rho it synchronises `stream` once (reading 84 bytes of
+ *     per-E counts back to the host).
+ */
+int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                        int64_t lib_begin, int64_t lib_count, const edm_params *params,
+                        float *rho, int64_t ld_rho, void *stream);
+
 /* Human-readable text for a status code (includes the CUDA error if any). */
 const char *edm_status_string(int status);
 
