@@ -238,7 +238,7 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
             a.rho_col0 = lb0;
             a.rho = rho;
             a.ld_rho = ld_rho;
-            if ((e = launch_lookup_chunked(a, E, tile_width(E, f16) == 64, st)) != cudaSuccess)
+            if ((e = launch_lookup_multi(a, st)) != cudaSuccess)
                 return EDM_ERR_CUDA;
         }
         tile0 += ntE;

@@ -93,7 +93,8 @@ int sm_count()
 
 // Budgets for the L2-resident working set of the cross-map phase.
 constexpr size_t kTileBlockBytes = 64ull << 20;  // target tiles per block
-constexpr size_t kTableBytes = 48ull << 20;      // kNN tables per library block
+constexpr size_t kTableBytes = 48ull << 20;      // kNN tables per library block (L2 target)
+constexpr int64_t kMinLibBlock = 256;            // library block floor
 
 int tq_pad(int64_t T, const edm_params *p) { return (int)(((T - p->Tp) + 31) / 32 * 32); }
 
@@ -121,7 +122,8 @@ edm::TableLayout make_layout(uint32_t sel, int64_t T, const edm_params *p)
 struct CcmWs {
     size_t pi, omom, meta, tiles, tables, total;
     int64_t n_tiles_max;
-    size_t table_bytes;
+    size_t table_bytes;  // L2-sized budget
+    size_t table_cap;    // allocated table area
 };
 
 CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
@@ -140,7 +142,8 @@ CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
     w.tables = off;
     edm::TableLayout all = make_layout((1u << EDM_MAX_E) - 1u, T, p);
     w.table_bytes = std::max(kTableBytes, (size_t)all.lib_stride);
-    off += align256(w.table_bytes);
+    w.table_cap = std::max(w.table_bytes, (size_t)std::min<int64_t>(N, kMinLibBlock) * (size_t)all.lib_stride);
+    off += align256(w.table_cap);
     w.total = off;
     return w;
 }
@@ -348,7 +351,11 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
         for (int t = tb0; t < tb0 + ntb; ++t)
             sel |= 1u << (tiles[(size_t)t].E - 1);
         const edm::TableLayout lay = make_layout(sel, T, params);
-        const int64_t per_block = std::min<int64_t>(65535, std::max<int64_t>(1, (int64_t)(L.table_bytes / (size_t)lay.lib_stride)));
+        // L2-sized library blocks; blocks of rare-E target blocks (many E,
+        // few tiles) may spill to HBM rather than shrink below kMinLibBlock
+        const int64_t per_block = std::min<int64_t>(
+            65535, std::max<int64_t>(std::min<int64_t>(kMinLibBlock, (int64_t)(L.table_cap / (size_t)lay.lib_stride)),
+                                     (int64_t)(L.table_bytes / (size_t)lay.lib_stride)));
         for (int64_t lb0 = 0; lb0 < lib_count; lb0 += per_block) {
             const int nlb = (int)std::min<int64_t>(per_block, lib_count - lb0);
             {
@@ -356,41 +363,46 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
                 EDM_CUDA(edm::launch_knn_tables(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
                                                 params->exclusion_radius, sel, lay, tables_d, st));
             }
-            // one launch per run of equal E inside the target block
-            for (int r0 = tb0; r0 < tb0 + ntb;) {
-                const int E = tiles[(size_t)r0].E;
-                const bool f16 = (tiles[(size_t)r0].flags & edm::kTileF16) != 0;
-                int r1 = r0;
-                int64_t targets = 0;
-                while (r1 < tb0 + ntb && tiles[(size_t)r1].E == E)
-                    targets += tiles[(size_t)r1++].count;
-                edm::LookupArgs a;
-                a.tiles = tiles_d;
-                a.meta = meta_d;
-                a.pi = pi_d;
-                a.omom = omom_d;
-                a.tables = tables_d;
-                a.lay = lay;
-                a.T = (int)T;
-                a.tau = params->tau;
-                a.Tp = params->Tp;
-                a.tile_begin = r0;
-                a.n_tiles = r1 - r0;
-                a.n_lib = nlb;
-                int parts = (4 * sms + a.n_tiles - 1) / a.n_tiles;
-                parts = std::max(1, std::min(parts, (nlb + 7) / 8));
-                a.lib_parts = parts;
-                a.rho_col0 = lb0;
-                a.rho = rho;
-                a.ld_rho = ld_rho;
-                {
-                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                    if (scalar)
-                        EDM_CUDA(edm::launch_lookup(a, E, st));
-                    else
-                        EDM_CUDA(edm::launch_lookup_chunked(a, E, f16, st));
+            int64_t targets = 0;
+            for (int t = tb0; t < tb0 + ntb; ++t)
+                targets += tiles[(size_t)t].count;
+            edm::LookupArgs a;
+            a.tiles = tiles_d;
+            a.meta = meta_d;
+            a.pi = pi_d;
+            a.omom = omom_d;
+            a.tables = tables_d;
+            a.lay = lay;
+            a.T = (int)T;
+            a.tau = params->tau;
+            a.Tp = params->Tp;
+            a.n_lib = nlb;
+            a.rho_col0 = lb0;
+            a.rho = rho;
+            a.ld_rho = ld_rho;
+            if (scalar) {
+                // comparison path: one launch per run of equal E
+                for (int r0 = tb0; r0 < tb0 + ntb;) {
+                    const int E = tiles[(size_t)r0].E;
+                    int r1 = r0;
+                    int64_t tg = 0;
+                    while (r1 < tb0 + ntb && tiles[(size_t)r1].E == E)
+                        tg += tiles[(size_t)r1++].count;
+                    a.tile_begin = r0;
+                    a.n_tiles = r1 - r0;
+                    int parts = (4 * sms + a.n_tiles - 1) / a.n_tiles;
+                    a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
+                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)tg * (double)nlb);
+                    EDM_CUDA(edm::launch_lookup(a, E, st));
+                    r0 = r1;
                 }
-                r0 = r1;
+            } else {
+                a.tile_begin = tb0;
+                a.n_tiles = ntb;
+                int parts = (4 * sms + ntb - 1) / ntb;
+                a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
+                LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
+                EDM_CUDA(edm::launch_lookup_multi(a, st));
             }
         }
     }

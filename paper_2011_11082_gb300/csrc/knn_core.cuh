@@ -11,9 +11,11 @@
 // real candidates meet is found cheaply -- from the previous E's list (each
 // of its entries' distance grows by one lag, recomputed in the same FP32
 // order as the lanes), from this E's list of earlier chunks, or, for the
-// first E, as the K-th smallest of the 32 lane minima.  Only the few
-// candidates at or below th are compacted (one ballot per register slot),
-// ranked by (d2, s) and kept as a sorted list carried to the next chunk.
+// first E, as the K-th smallest of the 32 lane minima.  Each lane marks its
+// slots at or below th in a bit mask; the few marked candidates have their
+// distance re-derived (same FP32 operation order, so bitwise equal to the
+// register), are ranked by (d2, s) and kept as a sorted list carried to the
+// next chunk.  The hot loop stays small: rare paths are out of line.
 // The list stores K+1 entries: the first K are the exact K smallest; the
 // extra one is a real candidate that lets the next E seed its threshold.
 //
@@ -49,7 +51,9 @@ struct KnnWarpScratch {
 struct KnnQuery {
     const float *xq;  // query series (shared memory)
     const float *xc;  // candidate series (shared memory); readable from
-                      // xc[-(E_lim-1)*tau] to xc[s_first + 32*J*chunks - 1]
+                      // xc[-(E_lim-1)*tau] to xc[s_first + 32*J*chunks - 1];
+                      // the padding holds +inf, so a candidate whose lag
+                      // falls before the series start gets distance +inf
     int t;            // query time in xq
     int s_first;      // first candidate time (slot 0)
     int s_last;       // last candidate time
@@ -78,6 +82,26 @@ __device__ __forceinline__ bool cand_ok(const KnnQuery &q, int s, int E)
     if (q.same && q.excl >= 0 && abs(s - q.t) <= q.excl)
         return false;
     return true;
+}
+
+// FP32 squared distance of candidate s at dimension E in the lanes'
+// operation order (zero start, one fma per lag, lags 0..E-1): bitwise equal
+// to the incrementally grown register value.
+__device__ __forceinline__ float dist32(const KnnQuery &q, int s, int E)
+{
+    float d = 0.f;
+    for (int m = 0; m < E; ++m) {
+        float diff = q.xq[q.t - m * q.tau] - q.xc[s - m * q.tau];
+        d = fmaf(diff, diff, d);
+    }
+    return d;
+}
+
+// K-th smallest of the 32 lane minima (every lane minimum is a real candidate).
+__device__ __noinline__ float kth_lane_min(float mn, int K)
+{
+    float srt = warp_sort_asc(mn);
+    return __shfl_sync(kFull, srt, K - 1);
 }
 
 // Rank-select: the buffer holds c (<= kCandCap) entries; write the cap
@@ -160,23 +184,43 @@ __device__ __forceinline__ unsigned long long buffer_kth_key(KnnWarpScratch &sc,
     return mine;
 }
 
-// Merge this chunk's candidates into the running list for E.  prevE is the
-// last E (< E) whose list was updated in this chunk, or 0.
-template <int J>
-__device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &sc, const float (&d2)[J], int c0, int E,
-                                            int prevE)
+// Append the marked candidates (bit j of m0/m1 = slot j) with key <= kth.
+__device__ __forceinline__ void append_marked(const KnnQuery &q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
+                                              int E, unsigned long long kth)
+{
+    const int lane = lane_id();
+    while (m0 | m1) {
+        int j;
+        if (m0) {
+            j = __ffs(m0) - 1;
+            m0 &= m0 - 1;
+        } else {
+            j = 32 + __ffs(m1) - 1;
+            m1 &= m1 - 1;
+        }
+        const int s = q.s_first + c0 + lane + 32 * j;
+        const float d = dist32(q, s, E);
+        if (dkey(d, s) <= kth) {
+            const int p = atomicAdd(&sc.cnt, 1);
+            if (p < kCandCap) {
+                sc.cd[p] = d;
+                sc.cs[p] = s;
+            }
+        }
+    }
+}
+
+// Threshold bound for the K-th smallest distance at E from the previous
+// selected E's list (its entries grown to dimension E), or +inf.
+__device__ __forceinline__ float seed_threshold(const KnnQuery &q, KnnWarpScratch &sc, int E, int prevE)
 {
     const int lane = lane_id();
     const int K = E + 1 + kGuard;
-    const int cap = K + 1;
-    const int lo = list_off(E);
-    const int have = sc.lcount[E];
-
     float th = CUDART_INF_F;
+    const int have = sc.lcount[E];
     if (have >= K)
-        th = sc.ld[lo + K - 1];
+        th = sc.ld[list_off(E) + K - 1];
     if (prevE > 0 && sc.lcount[prevE] >= K) {
-        // grow the previous list's distances to dimension E (same FP32 order)
         const int plo = list_off(prevE);
         float dv = 0.f;
         if (lane < K) {
@@ -196,37 +240,29 @@ __device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &s
             dv = fmaxf(dv, __shfl_xor_sync(kFull, dv, o));
         th = fminf(th, dv);
     }
-    if (th == CUDART_INF_F) {
-        float mn = CUDART_INF_F;
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-            mn = fminf(mn, d2[j]);
-        float srt = warp_sort_asc(mn);
-        th = __shfl_sync(kFull, srt, K - 1);
-    }
+    return th;
+}
 
-    // buffer := current list + chunk candidates with d2 <= th (ballot per slot)
+// Merge this chunk's marked candidates (d2 <= th) into the list for E.
+__device__ __noinline__ void merge_marked(const KnnQuery q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
+                                          int E)
+{
+    const int lane = lane_id();
+    const int K = E + 1 + kGuard;
+    const int cap = K + 1;
+    const int lo = list_off(E);
+    const int have = sc.lcount[E];
+
     if (lane < have) {
         sc.cd[lane] = sc.ld[lo + lane];
         sc.cs[lane] = sc.ls[lo + lane];
     }
-    const unsigned lt = (1u << lane) - 1u;
-    int base = have;
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        const bool p = d2[j] <= th;
-        const unsigned b = __ballot_sync(kFull, p);
-        if (b) {
-            const int pos = base + __popc(b & lt);
-            if (p && pos < kCandCap) {
-                sc.cd[pos] = d2[j];
-                sc.cs[pos] = q.s_first + c0 + lane + 32 * j;
-            }
-            base += __popc(b);
-        }
-    }
+    if (lane == 0)
+        sc.cnt = have;
     __syncwarp();
-    int c = base;
+    append_marked(q, sc, m0, m1, c0, E, ~0ull);
+    __syncwarp();
+    int c = sc.cnt;
     int tries = 0;
     while (c > kCandCap) {
         // Too many at the threshold: tighten it to the K-th smallest key of
@@ -242,17 +278,7 @@ __device__ __forceinline__ void merge_chunk(const KnnQuery &q, KnnWarpScratch &s
             sc.cs[p] = sc.ls[lo + lane];
         }
         __syncwarp();
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            int s = q.s_first + c0 + lane + 32 * j;
-            if (d2[j] <= th && dkey(d2[j], s) <= kth) {
-                int p = atomicAdd(&sc.cnt, 1);
-                if (p < kCandCap) {
-                    sc.cd[p] = d2[j];
-                    sc.cs[p] = s;
-                }
-            }
-        }
+        append_marked(q, sc, m0, m1, c0, E, kth);
         __syncwarp();
         c = sc.cnt;
         if (++tries >= 6 && c > kCandCap) {
@@ -310,7 +336,7 @@ __device__ __noinline__ void exhaustive64(const KnnQuery q, KnnWarpScratch &sc, 
 // Final neighbours of (query, E) with exact order; lanes n < k receive
 // (s_n, w_n) and call emit(E, k, s_n, w_n, lane < k).
 template <class Emit>
-__device__ __forceinline__ void finalize_E(const KnnQuery &q, KnnWarpScratch &sc, int E, Emit &emit)
+__device__ __noinline__ void finalize_E(const KnnQuery q, KnnWarpScratch &sc, int E, Emit &emit)
 {
     const int lane = lane_id();
     const int k = E + 1;
@@ -411,23 +437,33 @@ __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
         for (int E = 1; E <= q.E_lim; ++E) {
             const int off = (E - 1) * q.tau;
             const float xqv = q.xq[q.t - off];
-            // reads before the series start land in its zero padding; those
-            // candidates are not embeddable at this E and are dropped below
+            // lags before the series start read the +inf padding
             const float *xcj = q.xc + (q.s_first + c0 + lane - off);
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 float diff = xqv - xcj[32 * j];
                 d2[j] = fmaf(diff, diff, d2[j]);
             }
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                if (q.s_first + c0 + 32 * j >= off)
-                    break;
-                if (q.s_first + c0 + lane + 32 * j < off)
-                    d2[j] = CUDART_INF_F;
-            }
             if ((q.sel >> (E - 1)) & 1u) {
-                merge_chunk<J>(q, sc, d2, c0, E, prevE);
+                float th = seed_threshold(q, sc, E, prevE);
+                if (th == CUDART_INF_F) {
+                    float mn = CUDART_INF_F;
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        mn = fminf(mn, d2[j]);
+                    th = kth_lane_min(mn, E + 1 + kGuard);
+                }
+                unsigned m0 = 0u, m1 = 0u;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    if (d2[j] <= th) {
+                        if (j < 32)
+                            m0 |= 1u << j;
+                        else
+                            m1 |= 1u << (j - 32);
+                    }
+                }
+                merge_marked(q, sc, m0, m1, c0, E);
                 prevE = E;
             }
         }

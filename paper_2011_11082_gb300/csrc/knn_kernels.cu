@@ -10,7 +10,7 @@ namespace edm {
 constexpr int kKnnWarps = 8;
 constexpr int kKnnThreads = kKnnWarps * 32;
 
-// The staged series is padded: `front` zeros before it (reads of lags
+// The staged series is padded: `front` +inf values before it (reads of lags
 // before the series start) and 32*J + 4 after it (the tail of the last
 // candidate chunk).  front is a multiple of 4 floats.
 static int front_pad(int E_hi, int tau) { return ((E_hi - 1) * tau + 3) & ~3; }
@@ -31,12 +31,13 @@ static size_t knn_smem_bytes_exact(int T, int front, int J)
 
 int knn_max_T() { return (int)((200 * 1024 - kKnnWarps * sizeof(KnnWarpScratch) - 64) / sizeof(float)) - 32 * 48 - 1024; }
 
-// Stage series `src` (T floats) into xs[-front .. T + tail) with zero pads.
+// Stage series `src` (T floats) into xs[-front .. T + tail) with +inf
+// padding: a lag that falls outside the series makes the distance +inf.
 __device__ __forceinline__ void stage_series(float *xs_base, const float *__restrict__ src, int T, int front, int total)
 {
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         int t = i - front;
-        xs_base[i] = (t >= 0 && t < T) ? src[t] : 0.f;
+        xs_base[i] = (t >= 0 && t < T) ? src[t] : CUDART_INF_F;
     }
 }
 
@@ -224,7 +225,8 @@ struct EmitPublic {
 template <int J, bool kPublic>
 __global__ void __launch_bounds__(kKnnThreads, 2)
     knn_tables_kernel(const float *__restrict__ Y, int64_t ldY, int64_t lib0, int T, int tau, int Tp, int excl,
-                      uint32_t sel, int q_per_cta, int front, TableLayout lay, uint8_t *__restrict__ tables,
+                      uint32_t sel, int q_per_cta, int front, const __grid_constant__ TableLayout lay,
+                      uint8_t *__restrict__ tables,
                       int32_t *__restrict__ pub_idx, float *__restrict__ pub_w, int pub_E)
 {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -72,7 +72,8 @@ size_t lookup_smem_bytes(int T);
 cudaError_t launch_lookup(const LookupArgs &a, int E, cudaStream_t st);
 // 16-byte chunked gathers (FP32 or FP16 tiles); same contract.
 size_t chunked_smem_bytes(int T);
-cudaError_t launch_lookup_chunked(const LookupArgs &a, int E, bool f16, cudaStream_t st);
+// Tiles of any E / format in one launch (each CTA runs its tile's variant).
+cudaError_t launch_lookup_multi(const LookupArgs &a, cudaStream_t st);
 cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
                                     const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st);
 

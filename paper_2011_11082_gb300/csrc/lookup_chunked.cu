@@ -9,8 +9,10 @@
 // read eight different chunks, i.e. all 32 banks once, whatever the rows --
 // so the gathers run at full shared-memory bandwidth with one load and one
 // address operation per 4 (FP32) or 8 (FP16) target values.  Accumulation
-// is FP32 (Algorithm 5's weighted sum; then the rho moment sums); the FP16
-// form converts each gathered value to FP32 before use.
+// is FP32 (Algorithm 5's weighted sum; then the rho moment sums).  The FP16
+// form feeds the FP16 values straight into mixed-precision FMAs (FP16
+// operands, exact FP32 product, FP32 accumulator) with each weight split
+// into two FP16 halves w = hi + lo, so no separate conversion is issued.
 #include "edm_internal.cuh"
 #include "launchers.h"
 
@@ -42,6 +44,24 @@ __device__ __forceinline__ float2 h2f(uint32_t u)
     return __half22float2(h);
 }
 
+// pl += w * lo(u), ph += w * hi(u): FP16 operands, exact FP32 product,
+// FP32 accumulation (mixed-precision fma), no separate conversion.
+__device__ __forceinline__ void fma_h2(float &pl, float &ph, uint32_t u, uint16_t w)
+{
+    asm("{.reg .f16 l, h; mov.b32 {l, h}, %2; fma.rn.f32.f16 %0, l, %3, %0; fma.rn.f32.f16 %1, h, %3, %1;}"
+        : "+f"(pl), "+f"(ph)
+        : "r"(u), "h"(w));
+}
+
+// w = hi + lo with both halves in FP16 (relative error of hi + lo <= 2^-22).
+__device__ __forceinline__ void split_w(float w, uint16_t &hi, uint16_t &lo)
+{
+    const __half h = __float2half_rn(w);
+    const __half l = __float2half_rn(w - __half2float(h));
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(l);
+}
+
 // slot s of lane k at step c holds target 4*((k & 7) ^ c) + (s & 3) of the
 // set; target t of the set gathers slot ((t >> 2) ^ (k & 7)) * 4 + (t & 3)
 // from every lane k.
@@ -57,12 +77,14 @@ __device__ __forceinline__ float gather_slot_sum(const float *red, int t)
 }
 
 template <int K, bool F16>
-__global__ void __launch_bounds__(kCkThreads, 1) lookup_chunk_kernel(LookupArgs a)
+__device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 {
-    constexpr int NS = F16 ? 64 : 32;  // slots (targets) per lane
-    // prefetching the next row block's entries costs 2K registers; the FP16
-    // form (192 accumulators) affords it only for small K
-    constexpr bool kPref = F16 ? (K <= 4) : (K <= 16);
+    // FP16 tiles hold 64 targets per row: two passes over the row blocks,
+    // each covering four of the eight chunk positions (still 8 useful values
+    // per 16-byte load), keep 32 slots per lane per pass like FP32.
+    constexpr int PASSES = F16 ? 2 : 1;
+    constexpr int CPP = 8 / PASSES;  // chunk steps per pass
+    constexpr bool kPref = K <= 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
     const uint32_t pad = (128u - (raw & 127u)) & 127u;
@@ -99,123 +121,146 @@ __global__ void __launch_bounds__(kCkThreads, 1) lookup_chunk_kernel(LookupArgs 
         const uint8_t *lb = a.tables + (size_t)lib * a.lay.lib_stride;
         const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
         const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
-        float Sp[NS], Spp[NS], Spo[NS];
+        float tot[3][F16 ? 2 : 1];
 #pragma unroll
-        for (int r = 0; r < NS; ++r) {
-            Sp[r] = 0.f;
-            Spp[r] = 0.f;
-            Spo[r] = 0.f;
-        }
-        float wq[kPref ? K : 1];
-        uint32_t iq[kPref ? K : 1];
-        if (kPref) {
-            const bool v = lane < Tq;
+        for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
-            for (int n = 0; n < (kPref ? K : 1); ++n) {
-                wq[n] = v ? __ldg(Wt + n * tq_pad + lane) : 0.f;
-                iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane) : 0u;
+            for (int st = 0; st < (F16 ? 2 : 1); ++st)
+                tot[mm][st] = 0.f;
+#pragma unroll 1
+        for (int pass = 0; pass < PASSES; ++pass) {
+            const int c0 = pass * CPP;
+            float Sp[32], Spp[32], Spo[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                Sp[r] = 0.f;
+                Spp[r] = 0.f;
+                Spo[r] = 0.f;
             }
-        }
-        for (int b = 0; b < nblk; ++b) {
-            const int row = b * 32 + lane;
-            const bool valid = row < Tq;
-            float wn[K];
-            uint32_t Bn[K];
+            float wq[kPref ? K : 1];
+            uint32_t iq[kPref ? K : 1];
             if (kPref) {
+                const bool v = lane < Tq;
 #pragma unroll
                 for (int n = 0; n < (kPref ? K : 1); ++n) {
-                    wn[n] = wq[n];
-                    Bn[n] = base + iq[n] * 128u + lane16;
-                }
-                const int nrow = row + 32;
-                const bool v = nrow < Tq;
-#pragma unroll
-                for (int n = 0; n < (kPref ? K : 1); ++n) {
-                    wq[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
-                    iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
-                }
-            } else {
-#pragma unroll
-                for (int n = 0; n < K; ++n) {
-                    wn[n] = valid ? __ldg(Wt + n * tq_pad + row) : 0.f;
-                    Bn[n] = base + (valid ? (uint32_t)__ldg(It + n * tq_pad + row) : 0u) * 128u + lane16;
+                    wq[n] = v ? __ldg(Wt + n * tq_pad + lane) : 0.f;
+                    iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane) : 0u;
                 }
             }
-            const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
-            const uint32_t Bo = base + orow * 128u + lane16;
+            for (int b = 0; b < nblk; ++b) {
+                const int row = b * 32 + lane;
+                const bool valid = row < Tq;
+                float wn[K];
+                uint32_t Bn[K];
+                if (kPref) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const uint32_t x = (uint32_t)(c * 16);
-                if (!F16) {
-                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-                    for (int n = 0; n < K; ++n) {
-                        const float4 v = lds_v4(Bn[n] ^ x);
-                        p0 = fmaf(wn[n], v.x, p0);
-                        p1 = fmaf(wn[n], v.y, p1);
-                        p2 = fmaf(wn[n], v.z, p2);
-                        p3 = fmaf(wn[n], v.w, p3);
+                    for (int n = 0; n < (kPref ? K : 1); ++n) {
+                        wn[n] = wq[n];
+                        Bn[n] = base + iq[n] * 128u + lane16;
                     }
-                    const float4 o = lds_v4(Bo ^ x);
-                    const float pp[4] = {p0, p1, p2, p3};
-                    const float oo[4] = {o.x, o.y, o.z, o.w};
+                    const int nrow = row + 32;
+                    const bool v = nrow < Tq;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int s = c * 4 + i;
-                        Sp[s] += pp[i];
-                        Spp[s] = fmaf(pp[i], pp[i], Spp[s]);
-                        Spo[s] = fmaf(pp[i], oo[i], Spo[s]);
+                    for (int n = 0; n < (kPref ? K : 1); ++n) {
+                        wq[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
+                        iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
                     }
                 } else {
-                    float pl[4] = {0.f, 0.f, 0.f, 0.f}, ph[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int n = 0; n < K; ++n) {
-                        const uint4 u = lds_u4(Bn[n] ^ x);
-                        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+                        wn[n] = valid ? __ldg(Wt + n * tq_pad + row) : 0.f;
+                        Bn[n] = base + (valid ? (uint32_t)__ldg(It + n * tq_pad + row) : 0u) * 128u + lane16;
+                    }
+                }
+                const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
+                const uint32_t Bo = base + orow * 128u + lane16;
+                uint16_t whi[F16 ? K : 1], wlo[F16 ? K : 1];
+                if (F16) {
+#pragma unroll
+                    for (int n = 0; n < (F16 ? K : 1); ++n)
+                        split_w(wn[n], whi[n], wlo[n]);
+                }
+#pragma unroll
+                for (int cl = 0; cl < CPP; ++cl) {
+                    const uint32_t x = (uint32_t)((c0 + cl) * 16);
+                    if (!F16) {
+                        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+                        for (int n = 0; n < K; ++n) {
+                            const float4 v = lds_v4(Bn[n] ^ x);
+                            p0 = fmaf(wn[n], v.x, p0);
+                            p1 = fmaf(wn[n], v.y, p1);
+                            p2 = fmaf(wn[n], v.z, p2);
+                            p3 = fmaf(wn[n], v.w, p3);
+                        }
+                        const float4 o = lds_v4(Bo ^ x);
+                        const float pp[4] = {p0, p1, p2, p3};
+                        const float oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float2 f = h2f(uu[i]);
-                            pl[i] = fmaf(wn[n], f.x, pl[i]);
-                            ph[i] = fmaf(wn[n], f.y, ph[i]);
+                            const int sl = cl * 4 + i;
+                            Sp[sl] += pp[i];
+                            Spp[sl] = fmaf(pp[i], pp[i], Spp[sl]);
+                            Spo[sl] = fmaf(pp[i], oo[i], Spo[sl]);
                         }
-                    }
-                    const uint4 ou = lds_u4(Bo ^ x);
-                    const uint32_t oo[4] = {ou.x, ou.y, ou.z, ou.w};
+                    } else {
+                        float pl[4] = {0.f, 0.f, 0.f, 0.f}, ph[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float2 o = h2f(oo[i]);
-                        const int s = c * 4 + i;
-                        Sp[s] += pl[i];
-                        Spp[s] = fmaf(pl[i], pl[i], Spp[s]);
-                        Spo[s] = fmaf(pl[i], o.x, Spo[s]);
-                        Sp[32 + s] += ph[i];
-                        Spp[32 + s] = fmaf(ph[i], ph[i], Spp[32 + s]);
-                        Spo[32 + s] = fmaf(ph[i], o.y, Spo[32 + s]);
+                        for (int n = 0; n < K; ++n) {
+                            const uint4 u = lds_u4(Bn[n] ^ x);
+                            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                fma_h2(pl[i], ph[i], uu[i], whi[n]);
+                                fma_h2(pl[i], ph[i], uu[i], wlo[n]);
+                            }
+                        }
+                        const uint4 ou = lds_u4(Bo ^ x);
+                        const uint32_t oo[4] = {ou.x, ou.y, ou.z, ou.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float2 o = h2f(oo[i]);
+                            const int sl = cl * 4 + i;  // lo set: slots 0..15, hi set: 16..31
+                            Sp[sl] += pl[i];
+                            Spp[sl] = fmaf(pl[i], pl[i], Spp[sl]);
+                            Spo[sl] = fmaf(pl[i], o.x, Spo[sl]);
+                            Sp[16 + sl] += ph[i];
+                            Spp[16 + sl] = fmaf(ph[i], ph[i], Spp[16 + sl]);
+                            Spo[16 + sl] = fmaf(ph[i], o.y, Spo[16 + sl]);
+                        }
                     }
                 }
             }
-        }
-        // fold the per-(lane, slot) sums into per-target sums
+            // fold this pass's per-(lane, slot) sums into per-target sums:
+            // full slot c*4+i (c = chunk step 0..7) of each set
 #pragma unroll
-        for (int set = 0; set < NS / 32; ++set) {
-            float tot[3];
+            for (int st = 0; st < (F16 ? 2 : 1); ++st) {
 #pragma unroll
-            for (int mm = 0; mm < 3; ++mm) {
-                const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
+                for (int mm = 0; mm < 3; ++mm) {
+                    const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
 #pragma unroll
-                for (int r = 0; r < 32; ++r)
-                    red[r * kCkRed + lane] = S[set * 32 + r];
-                __syncwarp();
-                tot[mm] = gather_slot_sum(red, lane);
-                __syncwarp();
+                    for (int c = 0; c < 8; ++c)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const bool mine = c >= c0 && c < c0 + CPP;
+                            const int sl = (F16 ? st * 16 : 0) + ((c - c0) & (CPP - 1)) * 4 + i;
+                            red[(c * 4 + i) * kCkRed + lane] = mine ? S[sl] : 0.f;
+                        }
+                    __syncwarp();
+                    tot[mm][st] += gather_slot_sum(red, lane);
+                    __syncwarp();
+                }
             }
-            const int t = set * 32 + lane;
+        }
+#pragma unroll
+        for (int st = 0; st < (F16 ? 2 : 1); ++st) {
+            const int t = st * 32 + lane;
             if (t < m.count) {
                 const int64_t j = a.pi[m.first + t];
                 const float2 om = a.omom[m.first + t];
                 const float n = (float)Tq;
-                const float num = n * tot[2] - tot[0] * om.x;
-                const float den_p = n * tot[1] - tot[0] * tot[0];
+                const float num = n * tot[2][st] - tot[0][st] * om.x;
+                const float den_p = n * tot[1][st] - tot[0][st] * tot[0][st];
                 const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;
                 a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho;
             }
@@ -223,53 +268,57 @@ __global__ void __launch_bounds__(kCkThreads, 1) lookup_chunk_kernel(LookupArgs 
     }
 }
 
-template <class Kern>
-static cudaError_t launch_ck(Kern kern, const LookupArgs &a, cudaStream_t st)
+// One launch for a block of tiles of mixed E (and FP16/FP32 tiles): each
+// CTA runs the variant of its own tile, so a CTA only ever executes one
+// specialisation's code.
+__global__ void __launch_bounds__(kCkThreads, 1) lookup_multi_kernel(LookupArgs a)
 {
-    size_t smem = chunked_smem_bytes(a.T);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
-    kern<<<grid, kCkThreads, smem, st>>>(a);
-    return cudaGetLastError();
+    const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
+    const bool f16 = (m.flags & kTileF16) != 0;
+#define EDM_MK(KK)                                                                                                     \
+    case KK:                                                                                                           \
+        if (f16 && KK <= kF16MaxK)                                                                                     \
+            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true>(a);                                                     \
+        else                                                                                                           \
+            lookup_chunk_body<KK, false>(a);                                                                           \
+        break;
+    switch (m.E + 1) {
+        EDM_MK(2)
+        EDM_MK(3)
+        EDM_MK(4)
+        EDM_MK(5)
+        EDM_MK(6)
+        EDM_MK(7)
+        EDM_MK(8)
+        EDM_MK(9)
+        EDM_MK(10)
+        EDM_MK(11)
+        EDM_MK(12)
+        EDM_MK(13)
+        EDM_MK(14)
+        EDM_MK(15)
+        EDM_MK(16)
+        EDM_MK(17)
+        EDM_MK(18)
+        EDM_MK(19)
+        EDM_MK(20)
+        EDM_MK(21)
+    default: break;
+    }
+#undef EDM_MK
 }
 
-int chunked_max_k(bool f16) { return f16 ? kF16MaxK : EDM_MAX_E + 1; }
-
-#define EDM_CK_CASE(KK)                                                                                                \
-    case KK:                                                                                                           \
-        return f16 ? (KK <= kF16MaxK ? launch_ck(lookup_chunk_kernel<(KK <= kF16MaxK ? KK : 2), true>, a, st)          \
-                                     : cudaErrorInvalidValue)                                                          \
-                   : launch_ck(lookup_chunk_kernel<KK, false>, a, st);
-
-cudaError_t launch_lookup_chunked(const LookupArgs &a, int E, bool f16, cudaStream_t st)
+cudaError_t launch_lookup_multi(const LookupArgs &a, cudaStream_t st)
 {
     if (a.n_tiles <= 0 || a.n_lib <= 0)
         return cudaSuccess;
-    switch (E + 1) {
-        EDM_CK_CASE(2)
-        EDM_CK_CASE(3)
-        EDM_CK_CASE(4)
-        EDM_CK_CASE(5)
-        EDM_CK_CASE(6)
-        EDM_CK_CASE(7)
-        EDM_CK_CASE(8)
-        EDM_CK_CASE(9)
-        EDM_CK_CASE(10)
-        EDM_CK_CASE(11)
-        EDM_CK_CASE(12)
-        EDM_CK_CASE(13)
-        EDM_CK_CASE(14)
-        EDM_CK_CASE(15)
-        EDM_CK_CASE(16)
-        EDM_CK_CASE(17)
-        EDM_CK_CASE(18)
-        EDM_CK_CASE(19)
-        EDM_CK_CASE(20)
-        EDM_CK_CASE(21)
-    default: return cudaErrorInvalidValue;
-    }
+    size_t smem = chunked_smem_bytes(a.T);
+    cudaError_t e = cudaFuncSetAttribute(lookup_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
+    lookup_multi_kernel<<<grid, kCkThreads, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
