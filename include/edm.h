@@ -121,6 +121,23 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
 size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
 
 /*
+ * Both phases end to end with HOST buffers (the problem as the paper states
+ * it: series in, optimal E and the causal map out).  Copies Y to the device,
+ * runs phase 1, reads optE back, then phase 2 in blocks of `block` libraries
+ * whose target-major results stream back on a second stream while the next
+ * block computes.  Returns after everything has landed in host memory.
+ *   Y_host     [N][T] float32 (pinned memory gives full copy bandwidth)
+ *   optE_host  [N] int32 out
+ *   rho_host   [N][ld_rho] float32 out, target-major like edm_ccm_rho:
+ *              rho_host[j*ld_rho + i] = rho(library i -> target j); ld_rho >= N
+ *   block      libraries per block (<= 0: about 1 GiB of results per block)
+ *   ws         DEVICE workspace of edm_ccm_host_workspace_bytes(N, T, block, params)
+ */
+int edm_ccm_host(const float *Y_host, int64_t N, int64_t T, const edm_params *params, int32_t *optE_host,
+                 float *rho_host, int64_t ld_rho, int64_t block, void *ws, size_t ws_bytes, void *stream);
+size_t edm_ccm_host_workspace_bytes(int64_t N, int64_t T, int64_t block, const edm_params *params);
+
+/*
  * Adjoint of the cross map (not in the paper): given G = dL/d rho,
  * grad_Y = dL/dY for L = sum_ij G(i,j) rho(i,j), with every kNN index and
  * every optE held at the values the forward pass finds (the tables are

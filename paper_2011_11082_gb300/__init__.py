@@ -28,6 +28,7 @@ __all__ = [
     "edm_knn_table",
     "edm_ccm_rho",
     "edm_ccm_workspace_bytes",
+    "edm_ccm_host",
     "edm_ccm_rho_backward",
     "edm_ccm_backward_workspace_bytes",
     "ccm",
@@ -129,6 +130,30 @@ def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_cou
                          out.data_ptr(), _ld(out), workspace.data_ptr(), workspace.numel(), _stream(stream))
     _abi.check(st, "edm_ccm_rho")
     return out
+
+
+def edm_ccm_host(Y_host: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,
+                 precision: int = EDM_PRECISION_FP32, rho_out: torch.Tensor | None = None, block: int = 0,
+                 workspace: torch.Tensor | None = None, device=None, stream=None):
+    """Both phases with host buffers: (optE int32[N], rho target-major
+    float32[N][N]) in host memory.  Pass pinned tensors for full bandwidth."""
+    lib = _abi.load()
+    if Y_host.is_cuda or Y_host.dtype != torch.float32 or Y_host.dim() != 2 or not Y_host.is_contiguous():
+        raise TypeError("Y_host must be a contiguous float32 CPU tensor [N][T]")
+    N, T = Y_host.shape
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    optE = torch.empty(N, dtype=torch.int32, pin_memory=Y_host.is_pinned())
+    if rho_out is None:
+        rho_out = torch.empty((N, N), dtype=torch.float32, pin_memory=Y_host.is_pinned())
+    p = make_params(E_max=E_max, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    need = int(lib.edm_ccm_host_workspace_bytes(N, T, block, ctypes.byref(p)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    st = lib.edm_ccm_host(Y_host.data_ptr(), N, T, ctypes.byref(p), optE.data_ptr(), rho_out.data_ptr(),
+                          rho_out.stride(0), block, workspace.data_ptr(), workspace.numel(),
+                          _stream(stream if stream is not None else torch.cuda.current_stream(dev)))
+    _abi.check(st, "edm_ccm_host")
+    return optE, rho_out
 
 
 def edm_ccm_backward_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0) -> int:

@@ -43,6 +43,8 @@ SIGNATURES = {
     "edm_knn_table": (ctypes.c_int, [_vp, _i64, _i64, _i64, _i32, _pp, _vp, _vp, _i64, _vp]),
     "edm_ccm_rho": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i64, _i64, _pp, _vp, _i64, _vp, ctypes.c_size_t, _vp]),
     "edm_ccm_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _pp]),
+    "edm_ccm_host": (ctypes.c_int, [_vp, _i64, _i64, _pp, _vp, _vp, _i64, _i64, _vp, ctypes.c_size_t, _vp]),
+    "edm_ccm_host_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i64, _pp]),
     "edm_ccm_rho_noalloc": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i64, _i64, _pp, _vp, _i64, _vp]),
     "edm_ccm_rho_backward": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _i64, _pp, _vp, _vp, ctypes.c_size_t,
                                             _vp]),

@@ -34,10 +34,10 @@ struct NaLayout {
     int64_t n_tiles_max;
 };
 
-NaLayout na_layout(int64_t N, int64_t T)
+NaLayout na_layout(int64_t N, int64_t T, int RB)
 {
     NaLayout w;
-    w.n_tiles_max = (N + 31) / 32 + EDM_MAX_E;
+    w.n_tiles_max = (N + RB / 4 - 1) / (RB / 4) + EDM_MAX_E;
     size_t off = 0;
     w.counts = off;
     off += 256;
@@ -48,7 +48,7 @@ NaLayout na_layout(int64_t N, int64_t T)
     w.meta = off;
     off += al256((size_t)w.n_tiles_max * sizeof(TileMeta));
     w.tiles = off;
-    off += al256((size_t)w.n_tiles_max * (size_t)T * 128);
+    off += al256((size_t)w.n_tiles_max * (size_t)T * RB);
     w.tables = off;
     w.table_bytes = off < kStaticScratchBytes ? kStaticScratchBytes - off : 0;
     return w;
@@ -75,14 +75,14 @@ TableLayout na_table_layout(uint32_t sel, int64_t T, const edm_params *p)
     return lay;
 }
 
-int tile_width(int E, bool f16) { return (f16 && E + 1 <= kF16MaxK) ? 64 : 32; }
+int tile_width(int E, bool f16, int RB) { return (f16 && E + 1 <= kF16MaxK) ? RB / 2 : RB / 4; }
 
 }  // namespace
 
 // One CTA: count targets per E (counters cleared here), stable counting
 // sort of target indices by E into pi, and the tile list.  counts[0] flags
 // an optE value outside 1..EDM_MAX_E.
-__global__ void __launch_bounds__(1024) na_plan_kernel(const int32_t *__restrict__ optE, int N, int f16,
+__global__ void __launch_bounds__(1024) na_plan_kernel(const int32_t *__restrict__ optE, int N, int f16, int RB,
                                                        int32_t *__restrict__ counts, int32_t *__restrict__ pi,
                                                        TileMeta *__restrict__ meta)
 {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(1024) na_plan_kernel(const int32_t *__restrict
             start[E] = s;
             tstart[E] = ts;
             s += cnt[E];
-            const int w = (f16 && E + 1 <= kF16MaxK) ? 64 : 32;
+            const int w = (f16 && E + 1 <= kF16MaxK) ? RB / 2 : RB / 4;
             ts += (cnt[E] + w - 1) / w;
         }
         for (int E = 0; E <= EDM_MAX_E; ++E)
@@ -123,10 +123,11 @@ __global__ void __launch_bounds__(1024) na_plan_kernel(const int32_t *__restrict
             pos += __popc(b);
         }
         if (lane == 0) {
-            const int w = (f16 && E + 1 <= kF16MaxK) ? 64 : 32;
+            const bool wf16 = f16 && E + 1 <= kF16MaxK;
+            const int w = wf16 ? RB / 2 : RB / 4;
             int t = tstart[E];
             for (int c = 0; c < cnt[E]; c += w, ++t)
-                meta[t] = TileMeta{E, start[E] + c, min(w, cnt[E] - c), w == 64 ? kTileF16 : 0};
+                meta[t] = TileMeta{E, start[E] + c, min(w, cnt[E] - c), wf16 ? kTileF16 : 0};
         }
     }
 }
@@ -146,10 +147,11 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
         return EDM_ERR_INVALID;
     if (lib_begin < 0 || lib_count < 0 || lib_begin + lib_count > N || ld_rho < lib_count)
         return EDM_ERR_INVALID;
-    if (T > EDM_MAX_T || N > 0x7fffffffLL || T > knn_max_T() || chunked_smem_bytes((int)T) > 227u * 1024u)
+    if (T > EDM_MAX_T || N > 0x7fffffffLL || T > knn_max_T() || chunked_row_bytes((int)T) == 0)
         return EDM_ERR_UNSUPPORTED;
     const bool f16 = params->precision == EDM_PRECISION_FP16_TARGETS;
-    const NaLayout L = na_layout(N, T);
+    const int RB = chunked_row_bytes((int)T);
+    const NaLayout L = na_layout(N, T, RB);
     const TableLayout all = na_table_layout((1u << EDM_MAX_E) - 1u, T, params);
     // beyond the static array: reject before touching the device
     if (L.tables >= kStaticScratchBytes || L.table_bytes < (size_t)all.lib_stride)
@@ -177,7 +179,7 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
     unsigned char *tiles_d = ws + L.tiles;
     uint8_t *tables_d = ws + L.tables;
 
-    na_plan_kernel<<<1, 1024, 0, st>>>(optE, (int)N, f16 ? 1 : 0, counts_d, pi_d, meta_d);
+    na_plan_kernel<<<1, 1024, 0, st>>>(optE, (int)N, f16 ? 1 : 0, RB, counts_d, pi_d, meta_d);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return EDM_ERR_CUDA;
     int32_t counts[EDM_MAX_E + 1];
@@ -192,13 +194,13 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
         if (counts[E] > 0 && (T - params->Tp - (int64_t)(E - 1) * params->tau -
                               (params->exclusion_radius >= 0 ? 2 * (int64_t)params->exclusion_radius + 1 : 0)) < E + 1)
             return EDM_ERR_INVALID;
-        n_tiles += (counts[E] + tile_width(E, f16) - 1) / tile_width(E, f16);
+        n_tiles += (counts[E] + tile_width(E, f16, RB) - 1) / tile_width(E, f16, RB);
     }
     if ((e = launch_prep_targets(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles, (float *)tiles_d,
-                                 omom_d, st)) != cudaSuccess)
+                                 omom_d, st, RB)) != cudaSuccess)
         return EDM_ERR_CUDA;
     if (f16 && (e = launch_prep_targets_f16(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles, tiles_d,
-                                            omom_d, st)) != cudaSuccess)
+                                            omom_d, st, RB)) != cudaSuccess)
         return EDM_ERR_CUDA;
 
     int sms = 148;
@@ -207,7 +209,7 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
     // the table area of the static array
     int tile0 = 0;
     for (int E = 1; E <= EDM_MAX_E; ++E) {
-        const int ntE = (counts[E] + tile_width(E, f16) - 1) / tile_width(E, f16);
+        const int ntE = (counts[E] + tile_width(E, f16, RB) - 1) / tile_width(E, f16, RB);
         if (ntE == 0)
             continue;
         const uint32_t sel = 1u << (E - 1);
@@ -238,7 +240,7 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
             a.rho_col0 = lb0;
             a.rho = rho;
             a.ld_rho = ld_rho;
-            if ((e = launch_lookup_multi(a, st)) != cudaSuccess)
+            if ((e = launch_lookup_multi(a, RB, st)) != cudaSuccess)
                 return EDM_ERR_CUDA;
         }
         tile0 += ntE;

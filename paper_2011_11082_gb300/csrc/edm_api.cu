@@ -126,19 +126,30 @@ struct CcmWs {
     size_t table_cap;    // allocated table area
 };
 
+// Tile row bytes for a call: 128 (32 FP32 / 64 FP16 targets per row) when
+// a tile of T rows fits shared memory, else 64; the scalar path uses 128.
+int ccm_row_bytes(int64_t T, const edm_params *p)
+{
+    if (p->flags & EDM_FLAG_LOOKUP_SCALAR)
+        return 128;
+    int rb = edm::chunked_row_bytes((int)std::min<int64_t>(T, EDM_MAX_T));
+    return rb ? rb : 128;
+}
+
 CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
 {
     CcmWs w;
-    w.n_tiles_max = (N + 31) / 32 + EDM_MAX_E;
+    const int RB = ccm_row_bytes(T, p);
+    w.n_tiles_max = (N + RB / 4 - 1) / (RB / 4) + EDM_MAX_E;
     size_t off = 0;
     w.pi = off;
     off += align256((size_t)N * sizeof(int32_t));
     w.omom = off;
-    off += align256((size_t)w.n_tiles_max * 32 * sizeof(float2));
+    off += align256((size_t)N * sizeof(float2));
     w.meta = off;
     off += align256((size_t)w.n_tiles_max * sizeof(edm::TileMeta));
     w.tiles = off;
-    off += align256((size_t)w.n_tiles_max * (size_t)T * 32 * sizeof(float));
+    off += align256((size_t)w.n_tiles_max * (size_t)T * RB);
     w.tables = off;
     edm::TableLayout all = make_layout((1u << EDM_MAX_E) - 1u, T, p);
     w.table_bytes = std::max(kTableBytes, (size_t)all.lib_stride);
@@ -266,36 +277,49 @@ size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params)
     return ccm_ws_layout(N, T, params).total;
 }
 
-int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE, int64_t lib_begin,
-                int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, void *ws, size_t ws_bytes,
-                void *stream)
+}  // extern "C"
+
+namespace {
+
+// Host-side plan of the cross-map phase: targets grouped by E (stable),
+// tiles, and the device copies of the permutation and tile list.
+struct CcmPlan {
+    std::vector<edm::TileMeta> tiles;
+    int32_t *pi_d;
+    float2 *omom_d;
+    edm::TileMeta *meta_d;
+    float *tiles_d;
+    uint8_t *tables_d;
+    bool want_f16, scalar;
+    int RB;
+    CcmWs L;
+};
+
+int ccm_validate(int64_t N, int64_t T, int64_t ldY, const edm_params *params)
 {
     int rc = check_common(params);
     if (rc)
         return rc;
-    if (!Y || !optE || !rho || !ws || N < 1 || T < 2 || ldY < T)
-        return EDM_ERR_INVALID;
-    if (lib_begin < 0 || lib_count < 0 || lib_begin + lib_count > N || ld_rho < lib_count)
+    if (N < 1 || T < 2 || ldY < T)
         return EDM_ERR_INVALID;
     if (T > EDM_MAX_T || N > 0x7fffffffLL)
         return EDM_ERR_UNSUPPORTED;
     const bool scalar = (params->flags & EDM_FLAG_LOOKUP_SCALAR) != 0;
     if (scalar && params->precision != EDM_PRECISION_FP32)
         return EDM_ERR_INVALID;
-    if (T > edm::knn_max_T() ||
-        (scalar ? edm::lookup_smem_bytes((int)T) : edm::chunked_smem_bytes((int)T)) > 227u * 1024u)
+    if (T > edm::knn_max_T() || (scalar ? edm::lookup_smem_bytes((int)T) > 227u * 1024u : edm::chunked_row_bytes((int)T) == 0))
         return EDM_ERR_UNSUPPORTED;
-    const CcmWs L = ccm_ws_layout(N, T, params);
-    if (ws_bytes < L.total)
-        return EDM_ERR_WORKSPACE;
-    if (lib_count == 0)
-        return EDM_OK;
-    cudaStream_t st = (cudaStream_t)stream;
+    return EDM_OK;
+}
 
-    // --- plan: group the targets by their E (stable), tiles of 32 -------------
-    std::vector<int32_t> E_host((size_t)N);
-    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    EDM_CUDA(cudaStreamSynchronize(st));
+// Plan from host optE, upload it, stage the target tiles.
+int ccm_prepare(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *E_host, const edm_params *params,
+                void *ws, cudaStream_t st, CcmPlan &P)
+{
+    P.L = ccm_ws_layout(N, T, params);
+    const CcmWs &L = P.L;
+    P.scalar = (params->flags & EDM_FLAG_LOOKUP_SCALAR) != 0;
+    P.RB = ccm_row_bytes(T, params);
     int64_t count[EDM_MAX_E + 2] = {0};
     for (int64_t j = 0; j < N; ++j) {
         int E = E_host[(size_t)j];
@@ -313,36 +337,54 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
         for (int64_t j = 0; j < N; ++j)
             pi[(size_t)fill[E_host[(size_t)j]]++] = (int32_t)j;
     }
-    std::vector<edm::TileMeta> tiles;
-    const bool want_f16 = params->precision == EDM_PRECISION_FP16_TARGETS;
+    P.tiles.clear();
+    P.want_f16 = params->precision == EDM_PRECISION_FP16_TARGETS;
     for (int E = 1; E <= EDM_MAX_E; ++E) {
-        const bool f16 = want_f16 && E + 1 <= edm::kF16MaxK;
-        const int width = f16 ? 64 : 32;
+        const bool f16 = P.want_f16 && E + 1 <= edm::kF16MaxK;
+        const int width = f16 ? P.RB / 2 : P.RB / 4;
         for (int64_t c = 0; c < count[E]; c += width)
-            tiles.push_back(edm::TileMeta{E, (int)(start[E] + c), (int)std::min<int64_t>(width, count[E] - c),
-                                          f16 ? edm::kTileF16 : 0});
+            P.tiles.push_back(edm::TileMeta{E, (int)(start[E] + c), (int)std::min<int64_t>(width, count[E] - c),
+                                            f16 ? edm::kTileF16 : 0});
     }
-    const int n_tiles = (int)tiles.size();
-
+    const int n_tiles = (int)P.tiles.size();
     unsigned char *wsb = (unsigned char *)ws;
-    int32_t *pi_d = (int32_t *)(wsb + L.pi);
-    float2 *omom_d = (float2 *)(wsb + L.omom);
-    edm::TileMeta *meta_d = (edm::TileMeta *)(wsb + L.meta);
-    float *tiles_d = (float *)(wsb + L.tiles);
-    uint8_t *tables_d = (uint8_t *)(wsb + L.tables);
-    EDM_CUDA(cudaMemcpyAsync(pi_d, pi.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    EDM_CUDA(cudaMemcpyAsync(meta_d, tiles.data(), tiles.size() * sizeof(edm::TileMeta), cudaMemcpyHostToDevice, st));
+    P.pi_d = (int32_t *)(wsb + L.pi);
+    P.omom_d = (float2 *)(wsb + L.omom);
+    P.meta_d = (edm::TileMeta *)(wsb + L.meta);
+    P.tiles_d = (float *)(wsb + L.tiles);
+    P.tables_d = (uint8_t *)(wsb + L.tables);
+    EDM_CUDA(cudaMemcpyAsync(P.pi_d, pi.data(), (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    EDM_CUDA(cudaMemcpyAsync(P.meta_d, P.tiles.data(), P.tiles.size() * sizeof(edm::TileMeta), cudaMemcpyHostToDevice,
+                             st));
     {
         LaunchScope ls(EDM_KERNEL_PREP, st, (double)N);
-        EDM_CUDA(edm::launch_prep_targets(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles, tiles_d,
-                                          omom_d, st));
-        if (want_f16)
-            EDM_CUDA(edm::launch_prep_targets_f16(Y, ldY, (int)T, params->tau, params->Tp, pi_d, meta_d, n_tiles,
-                                                  (uint8_t *)tiles_d, omom_d, st));
+        EDM_CUDA(edm::launch_prep_targets(Y, ldY, (int)T, params->tau, params->Tp, P.pi_d, P.meta_d, n_tiles, P.tiles_d,
+                                          P.omom_d, st, P.RB));
+        if (P.want_f16)
+            EDM_CUDA(edm::launch_prep_targets_f16(Y, ldY, (int)T, params->tau, params->Tp, P.pi_d, P.meta_d, n_tiles,
+                                                  (uint8_t *)P.tiles_d, P.omom_d, st, P.RB));
     }
+    // (pageable sources are staged before cudaMemcpyAsync returns, so the
+    // host vectors may go away now)
+    return EDM_OK;
+}
 
+// Cross map of libraries [lib_begin, lib_begin + lib_count) into rho
+// (target-major, ld_rho) with a prepared plan.
+int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t ldY, int64_t lib_begin,
+                int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, cudaStream_t st)
+{
+    const CcmWs &L = P.L;
+    const std::vector<edm::TileMeta> &tiles = P.tiles;
+    const int n_tiles = (int)tiles.size();
+    const bool scalar = P.scalar;
+    int32_t *pi_d = P.pi_d;
+    float2 *omom_d = P.omom_d;
+    edm::TileMeta *meta_d = P.meta_d;
+    float *tiles_d = P.tiles_d;
+    uint8_t *tables_d = P.tables_d;
     // --- target blocks (L2-sized) x library blocks ------------------------------
-    const size_t tile_bytes = (size_t)T * 32 * sizeof(float);
+    const size_t tile_bytes = (size_t)T * P.RB;
     const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
     const int sms = sm_count();
     for (int tb0 = 0; tb0 < n_tiles; tb0 += tiles_per_block) {
@@ -402,10 +444,137 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
                 int parts = (4 * sms + ntb - 1) / ntb;
                 a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
                 LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                EDM_CUDA(edm::launch_lookup_multi(a, st));
+                EDM_CUDA(edm::launch_lookup_multi(a, P.RB, st));
             }
         }
     }
+    return EDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE, int64_t lib_begin,
+                int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, void *ws, size_t ws_bytes,
+                void *stream)
+{
+    int rc = ccm_validate(N, T, ldY, params);
+    if (rc)
+        return rc;
+    if (!Y || !optE || !rho || !ws)
+        return EDM_ERR_INVALID;
+    if (lib_begin < 0 || lib_count < 0 || lib_begin + lib_count > N || ld_rho < lib_count)
+        return EDM_ERR_INVALID;
+    if (ws_bytes < ccm_ws_layout(N, T, params).total)
+        return EDM_ERR_WORKSPACE;
+    if (lib_count == 0)
+        return EDM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> E_host((size_t)N);
+    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaStreamSynchronize(st));
+    CcmPlan P;
+    rc = ccm_prepare(Y, N, T, ldY, E_host.data(), params, ws, st, P);
+    if (rc)
+        return rc;
+    return ccm_execute(P, Y, N, T, ldY, lib_begin, lib_count, params, rho, ld_rho, st);
+}
+
+size_t edm_ccm_host_workspace_bytes(int64_t N, int64_t T, int64_t block, const edm_params *params)
+{
+    if (!params || N < 1 || T < 2)
+        return 0;
+    if (block <= 0)
+        block = std::min<int64_t>(N, std::max<int64_t>(256, (int64_t)((1ull << 30) / ((size_t)N * 4))));
+    return align256((size_t)N * T * 4) + align256((size_t)N * 4) + 2 * align256((size_t)N * block * 4) +
+           ccm_ws_layout(N, T, params).total;
+}
+
+int edm_ccm_host(const float *Y_host, int64_t N, int64_t T, const edm_params *params, int32_t *optE_host,
+                 float *rho_host, int64_t ld_rho, int64_t block, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc = ccm_validate(N, T, T, params);
+    if (rc)
+        return rc;
+    if (!Y_host || !optE_host || !rho_host || !ws || ld_rho < N)
+        return EDM_ERR_INVALID;
+    if (block <= 0)
+        block = std::min<int64_t>(N, std::max<int64_t>(256, (int64_t)((1ull << 30) / ((size_t)N * 4))));
+    block = std::min<int64_t>(block, N);
+    if (ws_bytes < edm_ccm_host_workspace_bytes(N, T, block, params))
+        return EDM_ERR_WORKSPACE;
+    const int64_t h = T / 2;
+    const int64_t span = (int64_t)(params->E_max - 1) * params->tau;
+    if (params->E_max < 1 || params->E_max > EDM_MAX_E || h - params->Tp - span < params->E_max + 1 ||
+        (T - h) - params->Tp - span < 2)
+        return EDM_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *w = (unsigned char *)ws;
+    float *Yd = (float *)w;
+    w += align256((size_t)N * T * 4);
+    int32_t *optE_d = (int32_t *)w;
+    w += align256((size_t)N * 4);
+    float *blk[2];
+    blk[0] = (float *)w;
+    w += align256((size_t)N * block * 4);
+    blk[1] = (float *)w;
+    w += align256((size_t)N * block * 4);
+    void *ccm_ws = w;
+
+    EDM_CUDA(cudaMemcpyAsync(Yd, Y_host, (size_t)N * T * 4, cudaMemcpyHostToDevice, st));
+    {
+        LaunchScope ls(EDM_KERNEL_SIMPLEX, st, (double)N);
+        EDM_CUDA(edm::launch_simplex(Yd, N, (int)T, T, params->E_max, params->tau, params->Tp, optE_d, nullptr, st));
+    }
+    EDM_CUDA(cudaMemcpyAsync(optE_host, optE_d, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaStreamSynchronize(st));
+    CcmPlan P;
+    rc = ccm_prepare(Yd, N, T, T, optE_host, params, ccm_ws, st, P);
+    if (rc)
+        return rc;
+    // library blocks: compute on `st`, copy back on a second stream while
+    // the next block computes (two device buffers)
+    cudaStream_t cp = nullptr;
+    cudaEvent_t done_c[2] = {nullptr, nullptr}, done_d[2] = {nullptr, nullptr};
+    cudaError_t e = cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&done_c[b], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&done_d[b], cudaEventDisableTiming);
+    }
+    int k = 0;
+    for (int64_t b0 = 0; b0 < N && e == cudaSuccess && rc == EDM_OK; b0 += block, ++k) {
+        const int64_t nb = std::min<int64_t>(block, N - b0);
+        const int buf = k & 1;
+        if (k >= 2 && (e = cudaStreamWaitEvent(st, done_d[buf], 0)) != cudaSuccess)
+            break;
+        rc = ccm_execute(P, Yd, N, T, T, b0, nb, params, blk[buf], nb, st);
+        if (rc)
+            break;
+        if ((e = cudaEventRecord(done_c[buf], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cp, done_c[buf], 0)) != cudaSuccess)
+            break;
+        e = cudaMemcpy2DAsync(rho_host + b0, (size_t)ld_rho * 4, blk[buf], (size_t)nb * 4, (size_t)nb * 4, (size_t)N,
+                              cudaMemcpyDeviceToHost, cp);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(done_d[buf], cp);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(cp);
+    if (e == cudaSuccess)
+        e = e2;
+    for (int b = 0; b < 2; ++b) {
+        if (done_c[b])
+            cudaEventDestroy(done_c[b]);
+        if (done_d[b])
+            cudaEventDestroy(done_d[b]);
+    }
+    if (cp)
+        cudaStreamDestroy(cp);
+    if (rc)
+        return rc;
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    EDM_CUDA(cudaStreamSynchronize(st));
     return EDM_OK;
 }
 

@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
     knn_tables_kernel(const float *__restrict__ Y, int64_t ldY, int64_t lib0, int T, int tau, int Tp, int excl,
                       uint32_t sel, int q_per_cta, int front, const __grid_constant__ TableLayout lay,
                       uint8_t *__restrict__ tables,
-                      int32_t *__restrict__ pub_idx, float *__restrict__ pub_w, int pub_E)
+                      int32_t *__restrict__ pub_idx, float *__restrict__ pub_w, int pub_E,
+                      const uint32_t *__restrict__ sel_dev)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int total = (int)series_floats(T, front, J);
@@ -240,6 +241,10 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
 
     const int warp = warp_id();
     KnnWarpScratch &sc = scratch[warp];
+    if (sel_dev)
+        sel &= *sel_dev;  // E set planned on the device
+    if (!sel)
+        return;
     const int E_hi = 32 - __clz(sel);  // highest selected E
     int E_lo = __ffs(sel);             // lowest selected E
     const int t_first = max(blockIdx.x * q_per_cta, (E_lo - 1) * tau);
@@ -322,7 +327,7 @@ cudaError_t launch_simplex(const float *Y, int64_t N, int T, int64_t ldY, int E_
 template <int J, bool kPublic>
 static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
                          uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw, int pE,
-                         cudaStream_t st)
+                         cudaStream_t st, int q_per_cta, const uint32_t *sel_dev)
 {
     const int E_hi = 32 - __builtin_clz(sel);
     const int front = front_pad(E_hi, tau);
@@ -331,30 +336,31 @@ static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, i
         cudaFuncSetAttribute(knn_tables_kernel<J, kPublic>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    const int q_per_cta = 64;
     dim3 grid((unsigned)((T - Tp + q_per_cta - 1) / q_per_cta), (unsigned)n_lib);
     knn_tables_kernel<J, kPublic><<<grid, kKnnThreads, smem, st>>>(Y, ldY, lib0, T, tau, Tp, excl, sel, q_per_cta,
-                                                                    front, lay, tables, pidx, pw, pE);
+                                                                    front, lay, tables, pidx, pw, pE, sel_dev);
     return cudaGetLastError();
 }
 
 template <bool kPublic>
 static cudaError_t knn_dispatch(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
                                 uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw,
-                                int pE, cudaStream_t st)
+                                int pE, cudaStream_t st, int q = 64, const uint32_t *sel_dev = nullptr)
 {
     switch (pick_J(T - Tp)) {
-    case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st);
-    case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st);
-    case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st);
-    default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st);
+    case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
     }
 }
 
 cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
-                              uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st)
+                              uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st, int q_per_cta,
+                              const uint32_t *sel_dev)
 {
-    return knn_dispatch<false>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, nullptr, nullptr, 1, st);
+    return knn_dispatch<false>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, nullptr, nullptr, 1, st,
+                               q_per_cta, sel_dev);
 }
 
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,

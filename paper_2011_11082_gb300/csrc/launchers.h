@@ -28,8 +28,11 @@ struct TableLayout {
 
 // Phase 2 tables for n_lib libraries (series lib0 .. lib0+n_lib-1 of Y)
 // for every E whose bit is set in sel, written in the internal layout.
+// q_per_cta: query points per CTA; sel_dev (optional): device word ANDed
+// into sel (E set planned on the device).
 cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
-                              uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st);
+                              uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
+                              int q_per_cta = 64, const uint32_t *sel_dev = nullptr);
 
 // Public table format: idx int32 [n_lib][Tq][E+1] (unshifted), w float [n_lib][Tq][E+1].
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
@@ -48,8 +51,10 @@ struct TileMeta {
     int flags;  // kTileF16
 };
 
+// RB: tile row bytes (128: 32 targets, 64: 16 targets per row)
 cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
-                                const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st);
+                                const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st,
+                                int RB = 128);
 
 struct LookupArgs {
     const float *tiles;
@@ -70,12 +75,15 @@ struct LookupArgs {
 size_t lookup_smem_bytes(int T);
 // All tiles in [tile_begin, tile_begin + n_tiles) must have this E.
 cudaError_t launch_lookup(const LookupArgs &a, int E, cudaStream_t st);
-// 16-byte chunked gathers (FP32 or FP16 tiles); same contract.
-size_t chunked_smem_bytes(int T);
+// 16-byte chunked gathers (FP32 or FP16 tiles) with RB-byte tile rows.
+size_t chunked_smem_bytes(int T, int RB);
+// Widest tile row (128 or 64 bytes) whose tile fits shared memory; 0: none.
+int chunked_row_bytes(int T);
 // Tiles of any E / format in one launch (each CTA runs its tile's variant).
-cudaError_t launch_lookup_multi(const LookupArgs &a, cudaStream_t st);
+cudaError_t launch_lookup_multi(const LookupArgs &a, int RB, cudaStream_t st);
 cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
-                                    const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st);
+                                    const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st,
+                                    int RB = 128);
 
 // Adjoint (backward.cu).
 struct BwArgs {

@@ -13,6 +13,8 @@
 // form feeds the FP16 values straight into mixed-precision FMAs (FP16
 // operands, exact FP32 product, FP32 accumulator) with each weight split
 // into two FP16 halves w = hi + lo, so no separate conversion is issued.
+#pragma once
+
 #include "edm_internal.cuh"
 #include "launchers.h"
 
@@ -21,8 +23,6 @@ namespace edm {
 constexpr int kCkWarps = 8;
 constexpr int kCkThreads = kCkWarps * 32;
 constexpr int kCkRed = 33;
-
-size_t chunked_smem_bytes(int T) { return 128 + (size_t)T * 128 + (size_t)kCkWarps * 32 * kCkRed * 4; }
 
 __device__ __forceinline__ float4 lds_v4(uint32_t addr)
 {
@@ -62,34 +62,50 @@ __device__ __forceinline__ void split_w(float w, uint16_t &hi, uint16_t &lo)
     lo = __half_as_ushort(l);
 }
 
-// slot s of lane k at step c holds target 4*((k & 7) ^ c) + (s & 3) of the
-// set; target t of the set gathers slot ((t >> 2) ^ (k & 7)) * 4 + (t & 3)
-// from every lane k.
+// Chunk position a lane starts from: with 128-byte rows the eight lanes of
+// a quarter-warp take positions 0..7; with 64-byte rows lanes pair up
+// (2l, 2l+1) on position l, so the observation loads (consecutive rows, of
+// alternating bank halves) stay conflict-free.
+template <int RB>
+__device__ __forceinline__ int lane_sub(int lane)
+{
+    return RB == 128 ? (lane & 7) : ((lane >> 1) & 3);
+}
+
+// Slot s of lane k at chunk step c holds target 4*(lane_sub(k) ^ c) + (s & 3)
+// of the set; target t of the set gathers slot ((t >> 2) ^ lane_sub(k)) * 4
+// + (t & 3) from every lane k.
+template <int RB>
 __device__ __forceinline__ float gather_slot_sum(const float *red, int t)
 {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const int slot = ((((t >> 2) ^ (k & 7)) << 2) | (t & 3));
+        const int slot = ((((t >> 2) ^ lane_sub<RB>(k)) << 2) | (t & 3));
         s += red[slot * kCkRed + k];
     }
     return s;
 }
 
-template <int K, bool F16>
+template <int K, bool F16, int RB>
 __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 {
-    // FP16 tiles hold 64 targets per row: two passes over the row blocks,
-    // each covering four of the eight chunk positions (still 8 useful values
-    // per 16-byte load), keep 32 slots per lane per pass like FP32.
-    constexpr int PASSES = F16 ? 2 : 1;
-    constexpr int CPP = 8 / PASSES;  // chunk steps per pass
+    // RB-byte rows hold RB/16 chunks; FP32 chunks are 4 targets, FP16 chunks
+    // 4 words = 8 targets (word w = targets w and w + RB/4).  FP16 with
+    // 128-byte rows makes two passes over the row blocks, each covering half
+    // of the chunk positions (still 8 useful values per 16-byte load), so a
+    // lane keeps at most 32 slots per pass.
+    constexpr int CR = RB / 16;                    // chunks per row
+    constexpr int PASSES = (F16 && RB == 128) ? 2 : 1;
+    constexpr int CPP = CR / PASSES;               // chunk steps per pass
+    constexpr int SET = CR * 4;                    // targets per set (lo / hi)
+    constexpr int HS = CPP * 4;                    // first hi slot (FP16)
     constexpr bool kPref = K <= 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
     const uint32_t pad = (128u - (raw & 127u)) & 127u;
     unsigned char *smem = smem_raw + pad;
-    float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * 128);
+    float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * RB);
     const uint32_t base = raw + pad;
 
     const int tile = a.tile_begin + blockIdx.x;
@@ -101,9 +117,9 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 
     {
         const float4 *src = reinterpret_cast<const float4 *>(
-            reinterpret_cast<const unsigned char *>(a.tiles) + (size_t)tile * a.T * 128);
+            reinterpret_cast<const unsigned char *>(a.tiles) + (size_t)tile * a.T * RB);
         float4 *dst = reinterpret_cast<float4 *>(smem);
-        const int n4 = a.T * 8;
+        const int n4 = a.T * (RB / 16);
         for (int i = threadIdx.x; i < n4; i += blockDim.x)
             dst[i] = __ldg(src + i);
     }
@@ -114,7 +130,7 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
     const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
     const int lib_lo = blockIdx.y * per;
     const int lib_hi = min(a.n_lib, lib_lo + per);
-    const uint32_t lane16 = (uint32_t)(lane & 7) * 16u;
+    const uint32_t lane16 = (uint32_t)lane_sub<RB>(lane) * 16u;
     const size_t tq_pad = (size_t)a.lay.Tq_pad;
 
     for (int lib = lib_lo + warp; lib < lib_hi; lib += kCkWarps) {
@@ -130,9 +146,9 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 #pragma unroll 1
         for (int pass = 0; pass < PASSES; ++pass) {
             const int c0 = pass * CPP;
-            float Sp[32], Spp[32], Spo[32];
+            float Sp[HS * (F16 ? 2 : 1)], Spp[HS * (F16 ? 2 : 1)], Spo[HS * (F16 ? 2 : 1)];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) {
+            for (int r = 0; r < HS * (F16 ? 2 : 1); ++r) {
                 Sp[r] = 0.f;
                 Spp[r] = 0.f;
                 Spo[r] = 0.f;
@@ -156,7 +172,7 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 #pragma unroll
                     for (int n = 0; n < (kPref ? K : 1); ++n) {
                         wn[n] = wq[n];
-                        Bn[n] = base + iq[n] * 128u + lane16;
+                        Bn[n] = base + iq[n] * (uint32_t)RB + lane16;
                     }
                     const int nrow = row + 32;
                     const bool v = nrow < Tq;
@@ -169,11 +185,11 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 #pragma unroll
                     for (int n = 0; n < K; ++n) {
                         wn[n] = valid ? __ldg(Wt + n * tq_pad + row) : 0.f;
-                        Bn[n] = base + (valid ? (uint32_t)__ldg(It + n * tq_pad + row) : 0u) * 128u + lane16;
+                        Bn[n] = base + (valid ? (uint32_t)__ldg(It + n * tq_pad + row) : 0u) * (uint32_t)RB + lane16;
                     }
                 }
                 const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
-                const uint32_t Bo = base + orow * 128u + lane16;
+                const uint32_t Bo = base + orow * (uint32_t)RB + lane16;
                 uint16_t whi[F16 ? K : 1], wlo[F16 ? K : 1];
                 if (F16) {
 #pragma unroll
@@ -220,42 +236,43 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const float2 o = h2f(oo[i]);
-                            const int sl = cl * 4 + i;  // lo set: slots 0..15, hi set: 16..31
+                            const int sl = cl * 4 + i;  // lo set: slots 0..HS-1, hi set: HS..
                             Sp[sl] += pl[i];
                             Spp[sl] = fmaf(pl[i], pl[i], Spp[sl]);
                             Spo[sl] = fmaf(pl[i], o.x, Spo[sl]);
-                            Sp[16 + sl] += ph[i];
-                            Spp[16 + sl] = fmaf(ph[i], ph[i], Spp[16 + sl]);
-                            Spo[16 + sl] = fmaf(ph[i], o.y, Spo[16 + sl]);
+                            Sp[HS + sl] += ph[i];
+                            Spp[HS + sl] = fmaf(ph[i], ph[i], Spp[HS + sl]);
+                            Spo[HS + sl] = fmaf(ph[i], o.y, Spo[HS + sl]);
                         }
                     }
                 }
             }
             // fold this pass's per-(lane, slot) sums into per-target sums:
-            // full slot c*4+i (c = chunk step 0..7) of each set
+            // full slot c*4+i (c = chunk step 0..CR-1) of each set
 #pragma unroll
             for (int st = 0; st < (F16 ? 2 : 1); ++st) {
 #pragma unroll
                 for (int mm = 0; mm < 3; ++mm) {
                     const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
+                    for (int c = 0; c < CR; ++c)
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const bool mine = c >= c0 && c < c0 + CPP;
-                            const int sl = (F16 ? st * 16 : 0) + ((c - c0) & (CPP - 1)) * 4 + i;
+                            const int sl = (F16 ? st * HS : 0) + ((c - c0) & (CPP - 1)) * 4 + i;
                             red[(c * 4 + i) * kCkRed + lane] = mine ? S[sl] : 0.f;
                         }
                     __syncwarp();
-                    tot[mm][st] += gather_slot_sum(red, lane);
+                    if (lane < SET)
+                        tot[mm][st] += gather_slot_sum<RB>(red, lane);
                     __syncwarp();
                 }
             }
         }
 #pragma unroll
         for (int st = 0; st < (F16 ? 2 : 1); ++st) {
-            const int t = st * 32 + lane;
-            if (t < m.count) {
+            const int t = st * SET + lane;
+            if (lane < SET && t < m.count) {
                 const int64_t j = a.pi[m.first + t];
                 const float2 om = a.omom[m.first + t];
                 const float n = (float)Tq;
@@ -266,131 +283,6 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
             }
         }
     }
-}
-
-// One launch for a block of tiles of mixed E (and FP16/FP32 tiles): each
-// CTA runs the variant of its own tile, so a CTA only ever executes one
-// specialisation's code.
-__global__ void __launch_bounds__(kCkThreads, 1) lookup_multi_kernel(LookupArgs a)
-{
-    const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
-    const bool f16 = (m.flags & kTileF16) != 0;
-#define EDM_MK(KK)                                                                                                     \
-    case KK:                                                                                                           \
-        if (f16 && KK <= kF16MaxK)                                                                                     \
-            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true>(a);                                                     \
-        else                                                                                                           \
-            lookup_chunk_body<KK, false>(a);                                                                           \
-        break;
-    switch (m.E + 1) {
-        EDM_MK(2)
-        EDM_MK(3)
-        EDM_MK(4)
-        EDM_MK(5)
-        EDM_MK(6)
-        EDM_MK(7)
-        EDM_MK(8)
-        EDM_MK(9)
-        EDM_MK(10)
-        EDM_MK(11)
-        EDM_MK(12)
-        EDM_MK(13)
-        EDM_MK(14)
-        EDM_MK(15)
-        EDM_MK(16)
-        EDM_MK(17)
-        EDM_MK(18)
-        EDM_MK(19)
-        EDM_MK(20)
-        EDM_MK(21)
-    default: break;
-    }
-#undef EDM_MK
-}
-
-cudaError_t launch_lookup_multi(const LookupArgs &a, cudaStream_t st)
-{
-    if (a.n_tiles <= 0 || a.n_lib <= 0)
-        return cudaSuccess;
-    size_t smem = chunked_smem_bytes(a.T);
-    cudaError_t e = cudaFuncSetAttribute(lookup_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
-    lookup_multi_kernel<<<grid, kCkThreads, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// FP16 staging: 64 targets per tile, z-normalised in FP64 then rounded to
-// FP16; the observation moments are taken over the rounded values (what the
-// lookup reads).  Tiles without the FP16 flag are left to the FP32 stager.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) prep_targets_f16_kernel(const float *__restrict__ Y, int64_t ldY, int T, int tau,
-                                                               int Tp, const int32_t *__restrict__ pi,
-                                                               const TileMeta *__restrict__ meta, uint8_t *__restrict__ tiles,
-                                                               float2 *__restrict__ omom)
-{
-    __shared__ float mu_s[64], inv_s[64];
-    const TileMeta m = meta[blockIdx.x];
-    if (!(m.flags & kTileF16))
-        return;
-    const int lane = lane_id(), warp = warp_id();
-    for (int slot = warp; slot < 64; slot += 8) {
-        double mu = 0.0, inv = 0.0;
-        if (slot < m.count) {
-            const float *y = Y + (int64_t)pi[m.first + slot] * ldY;
-            double acc = 0.0;
-            for (int t = lane; t < T; t += 32)
-                acc += (double)y[t];
-            mu = warp_sum_d(acc) / (double)T;
-            double v = 0.0;
-            for (int t = lane; t < T; t += 32) {
-                double d = (double)y[t] - mu;
-                v += d * d;
-            }
-            v = warp_sum_d(v) / (double)T;
-            inv = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
-            const float muf = (float)mu, invf = (float)inv;
-            const int L = (m.E - 1) * tau;
-            double so = 0.0, soo = 0.0;
-            for (int t = L + Tp + lane; t < T; t += 32) {
-                float z = __half2float(__float2half_rn((y[t] - muf) * invf));
-                so += (double)z;
-                soo += (double)z * (double)z;
-            }
-            so = warp_sum_d(so);
-            soo = warp_sum_d(soo);
-            if (lane == 0) {
-                double n = (double)(T - Tp - L);
-                omom[m.first + slot] = make_float2((float)so, (float)(n * soo - so * so));
-            }
-        }
-        if (lane == 0) {
-            mu_s[slot] = (float)mu;
-            inv_s[slot] = (float)inv;
-        }
-    }
-    __syncthreads();
-    uint32_t *tile = reinterpret_cast<uint32_t *>(tiles + (size_t)blockIdx.x * T * 128);
-    const float *ylo = lane < m.count ? Y + (int64_t)pi[m.first + lane] * ldY : nullptr;
-    const float *yhi = lane + 32 < m.count ? Y + (int64_t)pi[m.first + lane + 32] * ldY : nullptr;
-    const float mlo = mu_s[lane], ilo = inv_s[lane], mhi = mu_s[lane + 32], ihi = inv_s[lane + 32];
-    for (int t = warp; t < T; t += 8) {
-        float zl = ylo ? (ylo[t] - mlo) * ilo : 0.f;
-        float zh = yhi ? (yhi[t] - mhi) * ihi : 0.f;
-        __half2 h = __floats2half2_rn(zl, zh);
-        tile[(size_t)t * 32 + lane] = *reinterpret_cast<uint32_t *>(&h);
-    }
-}
-
-cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
-                                    const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st)
-{
-    if (n_tiles <= 0)
-        return cudaSuccess;
-    prep_targets_f16_kernel<<<n_tiles, 256, 0, st>>>(Y, ldY, T, tau, Tp, pi, meta, tiles, omom);
-    return cudaGetLastError();
 }
 
 }  // namespace edm

@@ -1,0 +1,158 @@
+// lookup_chunked128.cu -- the chunked lookup for 128-byte tile rows
+// (32 FP32 / 64 FP16 targets per row; series up to about 1,500 steps).
+#include "lookup_chunked.cuh"
+
+#define EDM_RB 128
+#define EDM_MULTI_NAME lookup_multi128_kernel
+#define EDM_MULTI_LAUNCH launch_lookup_multi128
+
+namespace edm {
+
+size_t chunked_smem_bytes(int T, int RB) { return 128 + (size_t)T * RB + (size_t)kCkWarps * 32 * kCkRed * 4; }
+
+// One launch for a block of tiles of mixed E (and FP16/FP32 tiles): each
+// CTA runs the variant of its own tile, so a CTA only ever executes one
+// specialisation's code.
+__global__ void __launch_bounds__(kCkThreads, 1) EDM_MULTI_NAME(LookupArgs a)
+{
+    const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
+    const bool f16 = (m.flags & kTileF16) != 0;
+#define EDM_MK(KK)                                                                                                     \
+    case KK:                                                                                                           \
+        if (f16 && KK <= kF16MaxK)                                                                                     \
+            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true, EDM_RB>(a);                                                     \
+        else                                                                                                           \
+            lookup_chunk_body<KK, false, EDM_RB>(a);                                                                           \
+        break;
+    switch (m.E + 1) {
+        EDM_MK(2)
+        EDM_MK(3)
+        EDM_MK(4)
+        EDM_MK(5)
+        EDM_MK(6)
+        EDM_MK(7)
+        EDM_MK(8)
+        EDM_MK(9)
+        EDM_MK(10)
+        EDM_MK(11)
+        EDM_MK(12)
+        EDM_MK(13)
+        EDM_MK(14)
+        EDM_MK(15)
+        EDM_MK(16)
+        EDM_MK(17)
+        EDM_MK(18)
+        EDM_MK(19)
+        EDM_MK(20)
+        EDM_MK(21)
+    default: break;
+    }
+#undef EDM_MK
+}
+
+cudaError_t EDM_MULTI_LAUNCH(const LookupArgs &a, cudaStream_t st)
+{
+    if (a.n_tiles <= 0 || a.n_lib <= 0)
+        return cudaSuccess;
+    size_t smem = chunked_smem_bytes(a.T, EDM_RB);
+    cudaError_t e = cudaFuncSetAttribute(EDM_MULTI_NAME, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
+    EDM_MULTI_NAME<<<grid, kCkThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP16 staging: 64 targets per tile, z-normalised in FP64 then rounded to
+// FP16; the observation moments are taken over the rounded values (what the
+// lookup reads).  Tiles without the FP16 flag are left to the FP32 stager.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) prep_targets_f16_kernel(const float *__restrict__ Y, int64_t ldY, int T, int tau,
+                                                               int Tp, const int32_t *__restrict__ pi,
+                                                               const TileMeta *__restrict__ meta, uint8_t *__restrict__ tiles,
+                                                               float2 *__restrict__ omom, int words)
+{
+    __shared__ float mu_s[64], inv_s[64];
+    const TileMeta m = meta[blockIdx.x];
+    if (!(m.flags & kTileF16))
+        return;
+    const int lane = lane_id(), warp = warp_id();
+    for (int slot = warp; slot < 64; slot += 8) {
+        double mu = 0.0, inv = 0.0;
+        if (slot < m.count) {
+            const float *y = Y + (int64_t)pi[m.first + slot] * ldY;
+            double acc = 0.0;
+            for (int t = lane; t < T; t += 32)
+                acc += (double)y[t];
+            mu = warp_sum_d(acc) / (double)T;
+            double v = 0.0;
+            for (int t = lane; t < T; t += 32) {
+                double d = (double)y[t] - mu;
+                v += d * d;
+            }
+            v = warp_sum_d(v) / (double)T;
+            inv = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+            const float muf = (float)mu, invf = (float)inv;
+            const int L = (m.E - 1) * tau;
+            double so = 0.0, soo = 0.0;
+            for (int t = L + Tp + lane; t < T; t += 32) {
+                float z = __half2float(__float2half_rn((y[t] - muf) * invf));
+                so += (double)z;
+                soo += (double)z * (double)z;
+            }
+            so = warp_sum_d(so);
+            soo = warp_sum_d(soo);
+            if (lane == 0) {
+                double n = (double)(T - Tp - L);
+                omom[m.first + slot] = make_float2((float)so, (float)(n * soo - so * so));
+            }
+        }
+        if (lane == 0) {
+            mu_s[slot] = (float)mu;
+            inv_s[slot] = (float)inv;
+        }
+    }
+    __syncthreads();
+    // rows of `words` 32-bit words; word w holds targets w and w + words
+    uint32_t *tile = reinterpret_cast<uint32_t *>(tiles + (size_t)blockIdx.x * T * words * 4);
+    if (lane < words) {
+        const float *ylo = lane < m.count ? Y + (int64_t)pi[m.first + lane] * ldY : nullptr;
+        const float *yhi = lane + words < m.count ? Y + (int64_t)pi[m.first + lane + words] * ldY : nullptr;
+        const float mlo = mu_s[lane], ilo = inv_s[lane], mhi = mu_s[lane + words], ihi = inv_s[lane + words];
+        for (int t = warp; t < T; t += 8) {
+            float zl = ylo ? (ylo[t] - mlo) * ilo : 0.f;
+            float zh = yhi ? (yhi[t] - mhi) * ihi : 0.f;
+            __half2 h = __floats2half2_rn(zl, zh);
+            tile[(size_t)t * words + lane] = *reinterpret_cast<uint32_t *>(&h);
+        }
+    }
+}
+
+cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
+                                    const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st,
+                                    int RB)
+{
+    if (n_tiles <= 0)
+        return cudaSuccess;
+    prep_targets_f16_kernel<<<n_tiles, 256, 0, st>>>(Y, ldY, T, tau, Tp, pi, meta, tiles, omom, RB / 4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_multi64(const LookupArgs &a, cudaStream_t st);
+
+cudaError_t launch_lookup_multi(const LookupArgs &a, int RB, cudaStream_t st)
+{
+    return RB == 128 ? launch_lookup_multi128(a, st) : launch_lookup_multi64(a, st);
+}
+
+int chunked_row_bytes(int T)
+{
+    if (chunked_smem_bytes(T, 128) <= 227u * 1024u)
+        return 128;
+    if (chunked_smem_bytes(T, 64) <= 227u * 1024u)
+        return 64;
+    return 0;
+}
+
+}  // namespace edm

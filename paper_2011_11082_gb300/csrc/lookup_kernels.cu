@@ -38,7 +38,7 @@ __device__ __forceinline__ float lds_f32(uint32_t addr)
 __global__ void __launch_bounds__(256) prep_targets_kernel(const float *__restrict__ Y, int64_t ldY, int T, int tau,
                                                            int Tp, const int32_t *__restrict__ pi,
                                                            const TileMeta *__restrict__ meta, float *__restrict__ tiles,
-                                                           float2 *__restrict__ omom)
+                                                           float2 *__restrict__ omom, int width)
 {
     __shared__ float mu_s[32], inv_s[32];
     const TileMeta m = meta[blockIdx.x];
@@ -82,13 +82,16 @@ __global__ void __launch_bounds__(256) prep_targets_kernel(const float *__restri
         }
     }
     __syncthreads();
-    float *tile = tiles + (size_t)blockIdx.x * T * 32;
+    // rows of `width` targets (32 for 128-byte rows, 16 for 64-byte rows)
+    float *tile = tiles + (size_t)blockIdx.x * T * width;
     const int slot = lane;
-    const float *y = slot < m.count ? Y + (int64_t)pi[m.first + slot] * ldY : nullptr;
-    const float muf = mu_s[slot], invf = inv_s[slot];
-    for (int t = warp; t < T; t += 8) {
-        float z = y ? (y[t] - muf) * invf : 0.f;
-        tile[(size_t)t * 32 + slot] = z;
+    if (slot < width) {
+        const float *y = slot < m.count ? Y + (int64_t)pi[m.first + slot] * ldY : nullptr;
+        const float muf = mu_s[slot], invf = inv_s[slot];
+        for (int t = warp; t < T; t += 8) {
+            float z = y ? (y[t] - muf) * invf : 0.f;
+            tile[(size_t)t * width + slot] = z;
+        }
     }
 }
 
@@ -320,11 +323,11 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_k_kernel(LookupArgs a)
 }
 
 cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
-                                const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st)
+                                const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st, int RB)
 {
     if (n_tiles <= 0)
         return cudaSuccess;
-    prep_targets_kernel<<<n_tiles, 256, 0, st>>>(Y, ldY, T, tau, Tp, pi, meta, tiles, omom);
+    prep_targets_kernel<<<n_tiles, 256, 0, st>>>(Y, ldY, T, tau, Tp, pi, meta, tiles, omom, RB / 4);
     return cudaGetLastError();
 }
 

@@ -204,3 +204,28 @@ def test_ccm_scalar_lookup_matches(edm):
     assert np.abs(got - R).max() < RHO_TOL
     got2 = edm.edm_ccm_rho(Yd, Ed).t().cpu().numpy()
     assert np.abs(got2 - R).max() < RHO_TOL
+
+
+def test_ccm_host_buffers_end_to_end(edm):
+    """edm_ccm_host: host series in, host optE and target-major rho out, in
+    several library blocks (copy-back overlapped with compute)."""
+    Y = synth.workload("n64_t500")
+    Yh = torch.from_numpy(Y).pin_memory()
+    optE, rho_t = edm.edm_ccm_host(Yh, E_max=10, block=24)
+    oE, _ = orc.optimal_E(Y, 10)
+    assert np.array_equal(optE.numpy(), oE)
+    R = orc.ccm_rho_rows(Y, oE)
+    assert np.abs(rho_t.numpy().T - R).max() < RHO_TOL
+
+
+def test_ccm_long_series_narrow_tiles(edm):
+    """T = 2,200 does not fit 128-byte tile rows: the 64-byte-row kernels
+    (16 FP32 / 32 FP16 targets per row) take over."""
+    Y = synth.coupled_logistic(45, 2200, 0.05, 0.05, seed_data=61, seed_noise=62)
+    oE = np.random.default_rng(8).integers(1, 14, size=45).astype(np.int32)
+    R = orc.ccm_rho_rows(Y, oE)
+    Yd, Ed = _dev(Y), torch.from_numpy(oE).cuda()
+    got = edm.edm_ccm_rho(Yd, Ed).t().cpu().numpy()
+    assert np.abs(got - R).max() < RHO_TOL
+    got16 = edm.edm_ccm_rho(Yd, Ed, precision=edm.EDM_PRECISION_FP16_TARGETS).t().cpu().numpy()
+    assert np.abs(got16 - R).max() < FP16_TOL
