@@ -40,6 +40,8 @@ WORKLOADS = {
     "n2048_t1500": (2048, 1500, 0.01, 0.02, 20),
     "n64_t500": (64, 500, 0.05, 0.05, 10),
 }
+# the batched form: 256 independent datasets, N ~ U[32, 1024], T ~ U[200, 3000]
+BATCHED = "batched256"
 METRIC = "cross-map pairs/s at N=101,729,T=1500 (1 GB300) + % HBM roofline vs plain FP32"
 UNIT = "pairs/s"
 
@@ -160,13 +162,88 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(args, lib, edm, _abi, torch, edm_synth):
+    """The batched form: every step runs both phases for 256 datasets of
+    uneven (N, T) through one replay of the captured CUDA graph."""
+    dev = torch.device("cuda", 0)
+    specs = edm_synth.batched_specs()
+    data = [edm_synth.batched_dataset(sp) for sp in specs]
+    prec = edm.EDM_PRECISION_FP16_TARGETS if args.precision == "fp16" else edm.EDM_PRECISION_FP32
+    Ys = [torch.from_numpy(Y).to(dev) for Y in data]
+    batch = edm.CCMBatch(Ys, E_max=20, precision=prec)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):  # the first run tunes and captures
+        batch.run()
+    torch.cuda.synchronize()
+    pairs = float(sum(Y.shape[0] ** 2 for Y in data))
+    launches0 = [lib.edm_launch_count(k) for k in range(_abi.EDM_KERNEL_BATCH)]
+    lib.edm_profile_enable(1)
+    lib.edm_profile_read(_abi.EDM_KERNEL_BATCH, None, None, None)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        batch.run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    lib.edm_profile_enable(0)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = sum(lib.edm_launch_count(k) - launches0[k] for k in range(_abi.EDM_KERNEL_BATCH))
+    m, n, u = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    lib.edm_profile_read(_abi.EDM_KERNEL_BATCH, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
+    peak, peak_kind = _peaks()
+    s_y = 2.0 if args.precision == "fp16" else 4.0
+    alg = sum(Y.shape[0] ** 2 * 4.0 + Y.shape[0] * Y.shape[1] * (4.0 + s_y) + 4.0 * Y.shape[0] for Y in data)
+    g_s = m.value / 1e3 / max(1, n.value)
+    achieved = alg / g_s / 1e9 if g_s > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": peak_kind, "kernel": "batched graph (all kernels of one replay)"}
+    # end to end: series in from pinned host memory, both phases, every rho
+    # map and optE back to pinned host memory, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Yh = [torch.from_numpy(Y).pin_memory() for Y in data]
+        Rh = [torch.empty((Y.shape[0], Y.shape[0]), dtype=torch.float32, pin_memory=True) for Y in data]
+        Eh = [torch.empty(Y.shape[0], dtype=torch.int32, pin_memory=True) for Y in data]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for Yd, Yp in zip(Ys, Yh):
+                Yd.copy_(Yp, non_blocking=True)
+            optE, rho = batch.run()
+            for a, b in zip(Rh, rho):
+                a.copy_(b, non_blocking=True)
+            for a, b in zip(Eh, optE):
+                a.copy_(b, non_blocking=True)
+            torch.cuda.synchronize()
+        ems = (time.perf_counter() - t0) * 1e3 / args.steps
+        e2e = {"value": pairs / (ems / 1e3), "unit": UNIT, "ms_per_step": ems,
+               "h2d_bytes_per_step": int(sum(Y.nbytes for Y in data)),
+               "d2h_bytes_per_step": int(sum(Y.shape[0] ** 2 * 4 + Y.shape[0] * 4 for Y in data)),
+               "host_buffers": "pinned", "api": "CCMBatch.run (edm_ccm_rho_batched)"}
+    line = {"metric": "cross-map pairs/s, batched form (256 datasets, 1 GB300)", "value": pairs / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f16-targets/f32-accumulate", "data": "synthetic",
+            "config": {"workload": BATCHED, "datasets": len(data), "pairs": pairs, "E_max": 20,
+                       "precision": args.precision, "graph": "one cudaGraphLaunch per step",
+                       "l2": "series 0.9 GB in total, rho 0.39 GB (rho alone exceeds L2)"},
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n101729_t1500", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="n101729_t1500", choices=sorted(WORKLOADS) + [BATCHED])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--lookup", default="chunked", choices=["chunked", "scalar"],
                     help="phase-2 gather kernels: 16-byte chunked (default) or scalar (comparison)")
@@ -196,6 +273,8 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     lib = _abi.load()
+    if args.workload == BATCHED:
+        return bench_batched(args, lib, edm, _abi, torch, edm_synth)
 
     N, T, dens, bmax, E_max = WORKLOADS[args.workload]
     # independent problems per rank (weak scaling): rank r uses data seed r

@@ -138,6 +138,49 @@ int edm_ccm_host(const float *Y_host, int64_t N, int64_t T, const edm_params *pa
 size_t edm_ccm_host_workspace_bytes(int64_t N, int64_t T, int64_t block, const edm_params *params);
 
 /*
+ * Batched form (not in the paper; the paper runs one dataset per job): many
+ * independent datasets of uneven N and T, each through both phases --
+ * optimal E (as edm_optimal_E) and its full causal map (as edm_ccm_rho with
+ * all N libraries) -- in ONE CUDA-graph launch.
+ *   sets      HOST array of n_sets descriptors (read during the call):
+ *               Y     [N][ldY] float32 device series of that dataset
+ *               optE  [N] int32 device out
+ *               rho   [N][ld_rho] float32 device out, target-major like
+ *                     edm_ccm_rho: rho[j*ld_rho + i] = rho(library i -> target j)
+ *   ws        device workspace of edm_ccm_rho_batched_workspace_bytes(...)
+ * Each dataset needs the edm_optimal_E length condition for params->E_max,
+ * N <= 65535, and T within what edm_ccm_rho accepts; the E grouping of its
+ * targets is planned on the device, so the call never synchronises with
+ * the GPU after its first use.
+ * First call with a given (sets, params, ws, ws_bytes): the library times
+ * candidate tile shapes on the batch's own data (kNN query points per CTA,
+ * lookup grid split; cached per series-length, size and precision class),
+ * then captures every launch of the batch -- datasets spread over parallel
+ * graph branches, each branch with its own workspace region -- into a CUDA
+ * graph and keeps the instantiated graph (up to 8, oldest dropped first).
+ * That first call synchronises `stream` and must not itself run inside a
+ * stream capture.  Later calls with identical arguments replay the graph
+ * with one cudaGraphLaunch on `stream`, asynchronously.  The cached graph
+ * holds the pointers it was captured with: reuse it only while those
+ * buffers stay allocated.
+ * The results are those of the per-dataset calls (same kernels and tile
+ * shapes within a dataset's tile).
+ */
+typedef struct edm_dataset {
+    const float *Y;
+    int64_t N, T, ldY;
+    int32_t *optE;
+    float *rho;
+    int64_t ld_rho;
+} edm_dataset;
+
+int edm_ccm_rho_batched(const edm_dataset *sets, int32_t n_sets, const edm_params *params, void *ws,
+                        size_t ws_bytes, void *stream);
+size_t edm_ccm_rho_batched_workspace_bytes(const edm_dataset *sets, int32_t n_sets, const edm_params *params);
+/* Drop every cached batched graph and tuning result (synchronises the device). */
+int edm_ccm_rho_batched_reset(void);
+
+/*
  * Adjoint of the cross map (not in the paper): given G = dL/d rho,
  * grad_Y = dL/dY for L = sum_ij G(i,j) rho(i,j), with every kNN index and
  * every optE held at the values the forward pass finds (the tables are
@@ -203,7 +246,9 @@ int edm_version(void);
 #define EDM_KERNEL_KNN 1     /* phase 2 kNN tables */
 #define EDM_KERNEL_PREP 2    /* target staging */
 #define EDM_KERNEL_LOOKUP 3  /* fused lookup + rho */
-#define EDM_KERNEL_COUNT 4
+#define EDM_KERNEL_PLAN 4    /* device-side E grouping (batched form) */
+#define EDM_KERNEL_BATCH 5   /* a whole batched graph (timed as one; units = pairs) */
+#define EDM_KERNEL_COUNT 6
 /*
  * edm_launch_count: launches of that kernel since load (always counted).
  * edm_profile_enable(1): from now on record a CUDA event pair on the

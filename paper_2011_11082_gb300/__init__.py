@@ -31,6 +31,8 @@ __all__ = [
     "edm_ccm_host",
     "edm_ccm_rho_backward",
     "edm_ccm_backward_workspace_bytes",
+    "edm_ccm_rho_batched",
+    "CCMBatch",
     "ccm",
     "ccm_rho_autograd",
     "CCMRhoFunction",
@@ -154,6 +156,63 @@ def edm_ccm_host(Y_host: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 
                           _stream(stream if stream is not None else torch.cuda.current_stream(dev)))
     _abi.check(st, "edm_ccm_host")
     return optE, rho_out
+
+
+class CCMBatch:
+    """Many datasets (uneven N, T) through both phases in one graph launch.
+
+    Holds the descriptors, the per-dataset outputs and the workspace, so that
+    every ``run()`` passes identical arguments to ``edm_ccm_rho_batched`` and
+    replays the CUDA graph captured on the first run.  ``optE[d]`` is int32
+    [N_d]; ``rho[d]`` is TARGET-MAJOR float32 [N_d][N_d] (``rho[d].t()`` is
+    the library-major map)."""
+
+    def __init__(self, Ys, E_max: int = 20, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,
+                 precision: int = EDM_PRECISION_FP32):
+        self.lib = _abi.load()
+        self.Ys = [_dev_f32(Y, f"Ys[{d}]") for d, Y in enumerate(Ys)]
+        if not self.Ys:
+            raise ValueError("empty batch")
+        dev = self.Ys[0].device
+        self.params = make_params(E_max=E_max, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius,
+                                  precision=precision)
+        self.optE = [torch.empty(Y.shape[0], dtype=torch.int32, device=dev) for Y in self.Ys]
+        self.rho = [torch.empty((Y.shape[0], Y.shape[0]), dtype=torch.float32, device=dev) for Y in self.Ys]
+        n = len(self.Ys)
+        self.sets = (_abi.edm_dataset * n)()
+        for d, Y in enumerate(self.Ys):
+            N, T = Y.shape
+            self.sets[d] = _abi.edm_dataset(Y.data_ptr(), N, T, _ld(Y), self.optE[d].data_ptr(),
+                                            self.rho[d].data_ptr(), N)
+        need = int(self.lib.edm_ccm_rho_batched_workspace_bytes(self.sets, n, ctypes.byref(self.params)))
+        if need == 0:
+            _abi.check(_abi.EDM_ERR_INVALID, "edm_ccm_rho_batched_workspace_bytes")
+        self.workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def run(self, stream=None):
+        st = self.lib.edm_ccm_rho_batched(self.sets, len(self.Ys), ctypes.byref(self.params),
+                                          self.workspace.data_ptr(), self.workspace.numel(), _stream(stream))
+        _abi.check(st, "edm_ccm_rho_batched")
+        return self.optE, self.rho
+
+    def mean_rho_grad(self):
+        """dL/dY_d for L = (sum over datasets and all pairs of rho) / sum_d N_d^2,
+        indices and optE frozen at the last run's values."""
+        total = float(sum(Y.shape[0] ** 2 for Y in self.Ys))
+        p = self.params
+        grads = []
+        for Y, E in zip(self.Ys, self.optE):
+            g = torch.full((Y.shape[0], Y.shape[0]), 1.0 / total, dtype=torch.float32, device=Y.device)
+            grads.append(edm_ccm_rho_backward(Y, E, g, tau=p.tau, Tp=p.Tp, exclusion_radius=p.exclusion_radius))
+        return grads
+
+
+def edm_ccm_rho_batched(Ys, E_max: int = 20, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,
+                        precision: int = EDM_PRECISION_FP32, stream=None):
+    """One-shot batched form: (list of optE, list of target-major rho).  Use
+    ``CCMBatch`` to replay the captured graph on repeated calls."""
+    return CCMBatch(Ys, E_max=E_max, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius,
+                    precision=precision).run(stream)
 
 
 def edm_ccm_backward_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0) -> int:

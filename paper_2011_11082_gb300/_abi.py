@@ -32,6 +32,18 @@ class edm_params(ctypes.Structure):
     ]
 
 
+class edm_dataset(ctypes.Structure):
+    _fields_ = [
+        ("Y", ctypes.c_void_p),
+        ("N", ctypes.c_int64),
+        ("T", ctypes.c_int64),
+        ("ldY", ctypes.c_int64),
+        ("optE", ctypes.c_void_p),
+        ("rho", ctypes.c_void_p),
+        ("ld_rho", ctypes.c_int64),
+    ]
+
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
@@ -49,6 +61,9 @@ SIGNATURES = {
     "edm_ccm_rho_backward": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _i64, _pp, _vp, _vp, ctypes.c_size_t,
                                             _vp]),
     "edm_ccm_backward_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _pp]),
+    "edm_ccm_rho_batched": (ctypes.c_int, [ctypes.POINTER(edm_dataset), _i32, _pp, _vp, ctypes.c_size_t, _vp]),
+    "edm_ccm_rho_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(edm_dataset), _i32, _pp]),
+    "edm_ccm_rho_batched_reset": (ctypes.c_int, []),
     "edm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "edm_last_cuda_error": (ctypes.c_int, []),
     "edm_version": (ctypes.c_int, []),
@@ -62,7 +77,11 @@ EDM_KERNEL_SIMPLEX = 0
 EDM_KERNEL_KNN = 1
 EDM_KERNEL_PREP = 2
 EDM_KERNEL_LOOKUP = 3
-KERNEL_NAMES = {0: "simplex_kernel", 1: "knn_tables_kernel", 2: "prep_targets_kernel", 3: "lookup_kernel"}
+EDM_KERNEL_PLAN = 4
+EDM_KERNEL_BATCH = 5
+EDM_KERNEL_COUNT = 6
+KERNEL_NAMES = {0: "simplex_kernel", 1: "knn_tables_kernel", 2: "prep_targets_kernel", 3: "lookup_kernel",
+                4: "batch_plan_kernel", 5: "batched_graph"}
 
 _lock = threading.Lock()
 _lib = None

@@ -33,7 +33,7 @@ struct ProfRec {
     int kernel;
     double units;
 };
-int64_t g_launches[EDM_KERNEL_COUNT] = {0, 0, 0, 0};
+int64_t g_launches[EDM_KERNEL_COUNT] = {};
 bool g_prof = false;
 std::vector<ProfRec> g_recs;
 double g_ms[EDM_KERNEL_COUNT], g_units[EDM_KERNEL_COUNT];
@@ -160,6 +160,20 @@ CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
 }
 
 }  // namespace
+
+namespace edm {
+void note_launches(int kernel, int64_t n) { g_launches[kernel] += n; }
+bool profiling() { return g_prof; }
+void prof_push(int kernel, cudaEvent_t a, cudaEvent_t b, double units)
+{
+    ProfRec r;
+    r.a = a;
+    r.b = b;
+    r.kernel = kernel;
+    r.units = units;
+    g_recs.push_back(r);
+}
+}  // namespace edm
 
 extern "C" {
 

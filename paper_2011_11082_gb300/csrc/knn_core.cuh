@@ -8,14 +8,15 @@
 // whose neighbour lists are wanted (Sec. III-B: one table per E, Algorithm 2).
 //
 // Selection per (query, E), K = E+1+kGuard: a threshold th that at least K
-// real candidates meet is found cheaply -- from the previous E's list (each
-// of its entries' distance grows by one lag, recomputed in the same FP32
-// order as the lanes), from this E's list of earlier chunks, or, for the
-// first E, as the K-th smallest of the 32 lane minima.  Each lane marks its
-// slots at or below th in a bit mask; the few marked candidates have their
-// distance re-derived (same FP32 operation order, so bitwise equal to the
-// register), are ranked by (d2, s) and kept as a sorted list carried to the
-// next chunk.  The hot loop stays small: rare paths are out of line.
+// real candidates meet -- the smaller of the previous E's list grown by one
+// lag (recomputed in the lanes' FP32 order), this E's list of earlier
+// chunks, and the K-th smallest of the 32 lane minima; if more candidates
+// than the buffer holds fall under it, counting rounds on the registers
+// lower it.  The distances go to a per-warp shared scratch, each lane marks
+// its slots at or below th in a bit mask, the marked candidates are
+// compacted (exclusive warp scan of per-lane counts), ranked by (d2, s) and
+// kept as a sorted list carried to the next chunk.  The hot loop stays
+// small: rare paths are out of line.
 // The list stores K+1 entries: the first K are the exact K smallest; the
 // extra one is a real candidate that lets the next E seed its threshold.
 //
@@ -35,7 +36,7 @@ namespace edm {
 __host__ __device__ constexpr int list_off(int E) { return (E - 1) * E / 2 + (E - 1) * (2 + kGuard); }
 constexpr int kListTotal = list_off(EDM_MAX_E + 1);
 
-struct KnnWarpScratch {
+struct __align__(16) KnnWarpScratch {
     float cd[kCandCap];
     int cs[kCandCap];
     float ld[kListTotal];
@@ -62,7 +63,12 @@ struct KnnQuery {
     int excl;
     int E_lim;        // distances are grown for E = 1..E_lim
     uint32_t sel;     // bit E-1: produce the neighbour list for E
+    float *d2s;       // this warp's distance scratch (shared): 32 * J floats,
+                      // slot j of lane l at d2s[(j/4)*128 + l*4 + j%4]
 };
+
+// Per-warp distance scratch bytes for J register slots per lane.
+__host__ __device__ constexpr size_t knn_d2s_bytes(int J) { return (size_t)32 * J * sizeof(float); }
 
 // FP64 squared distance in the reference's operation order.
 __device__ __forceinline__ double dist64(const float *xq, int t, const float *xc, int s, int E, int tau)
@@ -98,7 +104,7 @@ __device__ __forceinline__ float dist32(const KnnQuery &q, int s, int E)
 }
 
 // K-th smallest of the 32 lane minima (every lane minimum is a real candidate).
-__device__ __noinline__ float kth_lane_min(float mn, int K)
+__device__ __forceinline__ float kth_lane_min(float mn, int K)
 {
     float srt = warp_sort_asc(mn);
     return __shfl_sync(kFull, srt, K - 1);
@@ -184,32 +190,6 @@ __device__ __forceinline__ unsigned long long buffer_kth_key(KnnWarpScratch &sc,
     return mine;
 }
 
-// Append the marked candidates (bit j of m0/m1 = slot j) with key <= kth.
-__device__ __forceinline__ void append_marked(const KnnQuery &q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
-                                              int E, unsigned long long kth)
-{
-    const int lane = lane_id();
-    while (m0 | m1) {
-        int j;
-        if (m0) {
-            j = __ffs(m0) - 1;
-            m0 &= m0 - 1;
-        } else {
-            j = 32 + __ffs(m1) - 1;
-            m1 &= m1 - 1;
-        }
-        const int s = q.s_first + c0 + lane + 32 * j;
-        const float d = dist32(q, s, E);
-        if (dkey(d, s) <= kth) {
-            const int p = atomicAdd(&sc.cnt, 1);
-            if (p < kCandCap) {
-                sc.cd[p] = d;
-                sc.cs[p] = s;
-            }
-        }
-    }
-}
-
 // Threshold bound for the K-th smallest distance at E from the previous
 // selected E's list (its entries grown to dimension E), or +inf.
 __device__ __forceinline__ float seed_threshold(const KnnQuery &q, KnnWarpScratch &sc, int E, int prevE)
@@ -243,55 +223,116 @@ __device__ __forceinline__ float seed_threshold(const KnnQuery &q, KnnWarpScratc
     return th;
 }
 
-// Merge this chunk's marked candidates (d2 <= th) into the list for E.
-__device__ __noinline__ void merge_marked(const KnnQuery q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
-                                          int E)
+// Exclusive warp prefix sum of v; `total` receives the warp sum.
+__device__ __forceinline__ int warp_excl_scan(int v, int &total)
+{
+    const int lane = lane_id();
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o)
+            incl += u;
+    }
+    total = __shfl_sync(kFull, incl, 31);
+    return incl - v;
+}
+
+// Next marked slot of a lane (bit j of m0/m1 = slot j), clearing it.
+__device__ __forceinline__ int pop_slot(unsigned &m0, unsigned &m1)
+{
+    if (m0) {
+        const int j = __ffs(m0) - 1;
+        m0 &= m0 - 1;
+        return j;
+    }
+    const int j = 32 + __ffs(m1) - 1;
+    m1 &= m1 - 1;
+    return j;
+}
+
+// Distance of slot j of this lane as stored in the warp scratch (the
+// register value of the current E).
+__device__ __forceinline__ float stored_d2(const KnnQuery &q, int j)
+{
+    return q.d2s[(j >> 2) * 128 + lane_id() * 4 + (j & 3)];
+}
+
+// Write the marked candidates of this lane with key <= kth into the buffer
+// from position pos on (positions >= kCandCap are dropped).
+__device__ __forceinline__ void store_marked(const KnnQuery &q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
+                                             int pos, unsigned long long kth)
+{
+    const int lane = lane_id();
+    while (m0 | m1) {
+        const int j = pop_slot(m0, m1);
+        const int s = q.s_first + c0 + lane + 32 * j;
+        const float d = stored_d2(q, j);
+        if (dkey(d, s) <= kth) {
+            if (pos < kCandCap) {
+                sc.cd[pos] = d;
+                sc.cs[pos] = s;
+            }
+            ++pos;
+        }
+    }
+}
+
+// Marked candidates of this lane with key <= kth.
+__device__ __forceinline__ int count_marked(const KnnQuery &q, unsigned m0, unsigned m1, int c0,
+                                            unsigned long long kth)
+{
+    const int lane = lane_id();
+    int n = 0;
+    while (m0 | m1) {
+        const int j = pop_slot(m0, m1);
+        n += dkey(stored_d2(q, j), q.s_first + c0 + lane + 32 * j) <= kth;
+    }
+    return n;
+}
+
+// Rare path: the list plus the marked candidates exceed the buffer.  The
+// K-th smallest key of a buffered subset bounds the true K-th smallest
+// (the subset holds at least K real candidates), so keeping only keys at or
+// below it loses nothing; repeat until the survivors fit.
+__device__ __noinline__ int select_overflow(const KnnQuery q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
+                                            int E, int have)
 {
     const int lane = lane_id();
     const int K = E + 1 + kGuard;
-    const int cap = K + 1;
     const int lo = list_off(E);
-    const int have = sc.lcount[E];
-
-    if (lane < have) {
-        sc.cd[lane] = sc.ld[lo + lane];
-        sc.cs[lane] = sc.ls[lo + lane];
-    }
-    if (lane == 0)
-        sc.cnt = have;
-    __syncwarp();
-    append_marked(q, sc, m0, m1, c0, E, ~0ull);
-    __syncwarp();
-    int c = sc.cnt;
-    int tries = 0;
-    while (c > kCandCap) {
-        // Too many at the threshold: tighten it to the K-th smallest key of
-        // the buffered subset (all real candidates) and compact again.
-        unsigned long long kth = buffer_kth_key(sc, kCandCap, K);
+    unsigned long long kth = ~0ull;
+    int c = kCandCap + 1;
+    for (int tries = 0; tries < 6 && c > kCandCap; ++tries) {
+        // buffer := (list U marked) with key <= kth, truncated to kCandCap
+        const bool keep_l = lane < have && dkey(sc.ld[lo + lane], sc.ls[lo + lane]) <= kth;
+        int total;
+        const int mine = count_marked(q, m0, m1, c0, kth);
+        const int off = warp_excl_scan(mine, total);
+        const unsigned bl = __ballot_sync(kFull, keep_l);
+        const int nl = __popc(bl);
+        const float dl = keep_l ? sc.ld[lo + lane] : 0.f;
+        const int sl = keep_l ? sc.ls[lo + lane] : 0;
         __syncwarp();
+        if (keep_l) {
+            const int p = __popc(bl & ((1u << lane) - 1u));
+            sc.cd[p] = dl;
+            sc.cs[p] = sl;
+        }
+        store_marked(q, sc, m0, m1, c0, nl + off, kth);
+        __syncwarp();
+        c = nl + total;
+        if (c > kCandCap) {
+            kth = buffer_kth_key(sc, kCandCap, K);
+            __syncwarp();
+        }
+    }
+    if (c > kCandCap) {
         if (lane == 0)
-            sc.cnt = 0;
-        __syncwarp();
-        if (lane < have && dkey(sc.ld[lo + lane], sc.ls[lo + lane]) <= kth) {
-            int p = atomicAdd(&sc.cnt, 1);
-            sc.cd[p] = sc.ld[lo + lane];
-            sc.cs[p] = sc.ls[lo + lane];
-        }
-        __syncwarp();
-        append_marked(q, sc, m0, m1, c0, E, kth);
-        __syncwarp();
-        c = sc.cnt;
-        if (++tries >= 6 && c > kCandCap) {
-            if (lane == 0)
-                sc.ovf[E] = 1;
-            c = kCandCap;
-            break;
-        }
+            sc.ovf[E] = 1;
+        c = kCandCap;
     }
-    int kept = buffer_to_list(sc, c, cap, lo);
-    if (lane == 0)
-        sc.lcount[E] = kept;
-    __syncwarp();
+    return c;
 }
 
 // Exhaustive FP64 selection of the k nearest (rare fallback).
@@ -415,6 +456,100 @@ __device__ __noinline__ void finalize_E(const KnnQuery q, KnnWarpScratch &sc, in
     emit(E, k, s_n, w, lane < k);
 }
 
+// Candidates of the warp with d2 <= th (registers only).
+template <int J>
+__device__ __forceinline__ int count_le(const float (&d2)[J], float th)
+{
+    int n = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+        n += d2[j] <= th ? 1 : 0;
+    return __reduce_add_sync(kFull, (unsigned)n);
+}
+
+// Selection of one chunk for E (inline: the distance registers stay live
+// across it).  1) A threshold that at least K = E+3 real candidates meet:
+// the smaller of the grown previous list and the K-th smallest lane
+// minimum.  2) If more than the buffer holds are at or below it, tighten it
+// by counting rounds on the registers (the count of points within squared
+// radius th grows about linearly for points near a low-dimensional
+// attractor), keeping the count >= K.  3) Store
+// the distances to the warp scratch, compact the marked candidates behind
+// the list kept from earlier chunks (exclusive warp scan of per-lane
+// counts), and rank them into the list.
+template <int J>
+__device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, const float (&d2)[J], int c0, int E,
+                                         int prevE)
+{
+    const int lane = lane_id();
+    const int K = E + 1 + kGuard;
+    const int lo_l = list_off(E);
+    const int have = sc.lcount[E];
+    float mn = CUDART_INF_F;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+        mn = fminf(mn, d2[j]);
+    float th = fminf(seed_threshold(q, sc, E, prevE), kth_lane_min(mn, K));
+    th = fminf(th, 3.40282347e38f);  // never mark a +inf slot (not a candidate)
+    int c = have + count_le(d2, th);
+    if (c > kCandCap) {
+        // counting rounds; invariant: at least K real candidates (list
+        // entries of earlier chunks or this chunk's slots) are <= hi
+        float hi = th, lo = 0.f;
+        int c_hi = c - have;
+        const float want = (float)(K + 8);
+        for (int r = 0; r < 8 && have + c_hi > kCandCap; ++r) {
+            // the embedded points lie near a low-dimensional attractor, so
+            // the count grows about linearly in th (not like th^(E/2))
+            float g = lo > 0.f ? sqrtf(lo * hi) : hi * (want / (float)c_hi);
+            if (!(g < hi) || !(g > lo))
+                g = 0.5f * (lo + hi);
+            const int cg = count_le(d2, g);
+            const int lg = __popc(__ballot_sync(kFull, lane < have && sc.ld[lo_l + lane] <= g));
+            if (lg + cg >= K) {
+                hi = g;
+                c_hi = cg;
+            } else {
+                lo = g;
+            }
+        }
+        th = hi;
+        c = have + c_hi;
+    }
+    // distances of this E to the scratch (16-byte stores, conflict-free)
+#pragma unroll
+    for (int j4 = 0; j4 < J / 4; ++j4)
+        reinterpret_cast<float4 *>(q.d2s)[j4 * 32 + lane] =
+            make_float4(d2[4 * j4], d2[4 * j4 + 1], d2[4 * j4 + 2], d2[4 * j4 + 3]);
+    unsigned m0 = 0u, m1 = 0u;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        if (d2[j] <= th) {
+            if (j < 32)
+                m0 |= 1u << j;
+            else
+                m1 |= 1u << (j - 32);
+        }
+    }
+    __syncwarp();
+    if (c <= kCandCap) {
+        int total;
+        const int off = warp_excl_scan(__popc(m0) + __popc(m1), total);
+        if (lane < have) {
+            sc.cd[lane] = sc.ld[lo_l + lane];
+            sc.cs[lane] = sc.ls[lo_l + lane];
+        }
+        store_marked(q, sc, m0, m1, c0, have + off, ~0ull);
+        __syncwarp();
+    } else {
+        c = select_overflow(q, sc, m0, m1, c0, E, have);
+    }
+    const int kept = buffer_to_list(sc, c, K + 1, lo_l);
+    if (lane == 0)
+        sc.lcount[E] = kept;
+    __syncwarp();
+}
+
 // Full query: sweep all candidate chunks, then emit every selected E.
 template <int J, class Emit>
 __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
@@ -445,25 +580,7 @@ __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
                 d2[j] = fmaf(diff, diff, d2[j]);
             }
             if ((q.sel >> (E - 1)) & 1u) {
-                float th = seed_threshold(q, sc, E, prevE);
-                if (th == CUDART_INF_F) {
-                    float mn = CUDART_INF_F;
-#pragma unroll
-                    for (int j = 0; j < J; ++j)
-                        mn = fminf(mn, d2[j]);
-                    th = kth_lane_min(mn, E + 1 + kGuard);
-                }
-                unsigned m0 = 0u, m1 = 0u;
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    if (d2[j] <= th) {
-                        if (j < 32)
-                            m0 |= 1u << j;
-                        else
-                            m1 |= 1u << (j - 32);
-                    }
-                }
-                merge_marked(q, sc, m0, m1, c0, E);
+                select_E<J>(q, sc, d2, c0, E, prevE);
                 prevE = E;
             }
         }

@@ -17,19 +17,33 @@ static int front_pad(int E_hi, int tau) { return ((E_hi - 1) * tau + 3) & ~3; }
 
 __host__ __device__ static size_t series_floats(int T, int front, int J) { return ((size_t)front + T + 32 * J + 4 + 3) & ~(size_t)3; }
 
+// Shared memory: the padded series, then per warp a KnnWarpScratch, then
+// per warp the distance scratch of 32 * J floats.
 size_t knn_smem_bytes(int T, int warps)
 {
     // worst case: J = 48, front for E = EDM_MAX_E at tau = 1 (larger tau is
     // sized at launch)
-    return series_floats(T, front_pad(EDM_MAX_E, 1), 48) * sizeof(float) + (size_t)warps * sizeof(KnnWarpScratch) + 64;
+    return series_floats(T, front_pad(EDM_MAX_E, 1), 48) * sizeof(float) +
+           (size_t)warps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(48)) + 64;
 }
 
 static size_t knn_smem_bytes_exact(int T, int front, int J)
 {
-    return series_floats(T, front, J) * sizeof(float) + (size_t)kKnnWarps * sizeof(KnnWarpScratch) + 64;
+    return series_floats(T, front, J) * sizeof(float) +
+           (size_t)kKnnWarps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(J)) + 64;
 }
 
-int knn_max_T() { return (int)((200 * 1024 - kKnnWarps * sizeof(KnnWarpScratch) - 64) / sizeof(float)) - 32 * 48 - 1024; }
+int knn_max_T()
+{
+    return (int)((200 * 1024 - kKnnWarps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(48)) - 64) / sizeof(float)) -
+           32 * 48 - 1024;
+}
+
+// Distance scratch of warp w (behind the per-warp KnnWarpScratch array).
+__device__ __forceinline__ float *warp_d2s(KnnWarpScratch *scratch, int J)
+{
+    return reinterpret_cast<float *>(scratch + kKnnWarps) + (size_t)warp_id() * 32 * J;
+}
 
 // Stage series `src` (T floats) into xs[-front .. T + tail) with +inf
 // padding: a lag that falls outside the series makes the distance +inf.
@@ -142,6 +156,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2) simplex_kernel(const float *__
         q.excl = -1;
         q.E_lim = E_lim;
         q.sel = E_lim >= 32 ? 0xffffffffu : ((1u << E_lim) - 1u);
+        q.d2s = warp_d2s(scratch, J);
         emit.t = t;
         knn_query<J>(q, sc, emit);
     }
@@ -272,6 +287,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
         q.excl = excl;
         q.E_lim = E_lim;
         q.sel = s_t;
+        q.d2s = warp_d2s(scratch, J);
         if (kPublic) {
             ep.t = t;
             knn_query<J>(q, sc, ep);
@@ -290,6 +306,8 @@ static int pick_J(int n_slots)
         return 8;
     if (need <= 16)
         return 16;
+    if (need <= 24)
+        return 24;
     if (need <= 32)
         return 32;
     return 48;
@@ -319,6 +337,7 @@ cudaError_t launch_simplex(const float *Y, int64_t N, int T, int64_t ldY, int E_
     switch (pick_J(h - Tp)) {
     case 8: return simplex_J<8>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
     case 16: return simplex_J<16>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
+    case 24: return simplex_J<24>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
     case 32: return simplex_J<32>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
     default: return simplex_J<48>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
     }
@@ -350,6 +369,7 @@ static cudaError_t knn_dispatch(const float *Y, int64_t ldY, int64_t lib0, int n
     switch (pick_J(T - Tp)) {
     case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
     case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 24: return knn_J<24, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
     case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
     default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
     }

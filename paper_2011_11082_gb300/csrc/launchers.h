@@ -85,6 +85,12 @@ cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau,
                                     const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st,
                                     int RB = 128);
 
+// Launch accounting shared by the translation units (edm_api.cu).
+void note_launches(int kernel, int64_t n);
+bool profiling();
+// Takes ownership of the two events (destroyed by edm_profile_read).
+void prof_push(int kernel, cudaEvent_t a, cudaEvent_t b, double units);
+
 // Adjoint (backward.cu).
 struct BwArgs {
     const float *Y;

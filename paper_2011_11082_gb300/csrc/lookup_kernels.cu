@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(256) prep_targets_kernel(const float *__restri
 {
     __shared__ float mu_s[32], inv_s[32];
     const TileMeta m = meta[blockIdx.x];
-    if (m.flags & kTileF16)
-        return;  // staged by the FP16 kernel
+    if ((m.flags & kTileF16) || m.E == 0)
+        return;  // staged by the FP16 kernel, or an unused (planned-empty) tile
     const int lane = lane_id(), warp = warp_id();
     for (int slot = warp; slot < 32; slot += 8) {
         double mu = 0.0, inv = 0.0;

@@ -79,3 +79,27 @@ def test_workspace_grows_with_problem(lib):
     a = lib.edm_ccm_workspace_bytes(1000, 1500, ctypes.byref(p))
     b = lib.edm_ccm_workspace_bytes(100000, 1500, ctypes.byref(p))
     assert b > a > 1000 * 1500 * 4
+
+
+def test_batched_argument_checks_need_no_gpu(lib):
+    from paper_2011_11082_gb300 import make_params
+    from paper_2011_11082_gb300._abi import edm_dataset
+
+    p = make_params(E_max=10)
+    fake = 0x1000  # never dereferenced: checks fail first
+    sets = (edm_dataset * 2)(edm_dataset(fake, 64, 500, 500, fake, fake, 64),
+                             edm_dataset(fake, 300, 1200, 1216, fake, fake, 300))
+    need = lib.edm_ccm_rho_batched_workspace_bytes(sets, 2, ctypes.byref(p))
+    assert need > 0
+    # the batch needs at least the larger dataset's own tile and table space
+    assert need > lib.edm_ccm_rho_batched_workspace_bytes(sets, 1, ctypes.byref(p))
+    assert lib.edm_ccm_rho_batched(sets, 2, ctypes.byref(p), fake, need - 1, None) == 3
+    assert lib.edm_ccm_rho_batched(sets, 0, ctypes.byref(p), fake, need, None) == 1
+    assert lib.edm_ccm_rho_batched(sets, 2, ctypes.byref(p), None, need, None) == 1
+    bad = (edm_dataset * 1)(edm_dataset(fake, 64, 30, 30, fake, fake, 64))  # T too short for E_max
+    assert lib.edm_ccm_rho_batched_workspace_bytes(bad, 1, ctypes.byref(p)) == 0
+    assert lib.edm_ccm_rho_batched(bad, 1, ctypes.byref(p), fake, 1 << 30, None) == 1
+    narrow = (edm_dataset * 1)(edm_dataset(fake, 64, 500, 500, fake, fake, 63))  # ld_rho < N
+    assert lib.edm_ccm_rho_batched(narrow, 1, ctypes.byref(p), fake, 1 << 30, None) == 1
+    big = (edm_dataset * 1)(edm_dataset(fake, 70000, 500, 500, fake, fake, 70000))  # N beyond 16-bit grid
+    assert lib.edm_ccm_rho_batched(big, 1, ctypes.byref(p), fake, 1 << 40, None) == 5
