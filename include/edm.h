@@ -47,13 +47,19 @@ extern "C" {
 
 #define EDM_PRECISION_FP32 0         /* targets staged as float32 */
 #define EDM_PRECISION_FP16_TARGETS 1 /* targets staged as float16 (for E <= 11; larger
-                                        E stay float32), FP32 accumulation */
+                                        E stay float32); the FP32 table weights enter
+                                        each FMA as float16 copies; exact products,
+                                        FP32 accumulation */
 
 /* flags */
 #define EDM_FLAG_NONE 0u
 /* phase 2: use the scalar-gather lookup kernels instead of the 16-byte
    chunked ones (FP32 targets only; kept for comparison) */
 #define EDM_FLAG_LOOKUP_SCALAR 1u
+/* edm_optimal_E / edm_ccm_rho: first scan Y for non-finite values; if a
+   series holds one, return EDM_ERR_INVALID without computing and keep its
+   index for edm_last_bad_series().  The scan synchronises `stream`. */
+#define EDM_FLAG_VALIDATE 2u
 
 typedef struct edm_params {
     int32_t E_max;            /* phase 1 searches E = 1..E_max (<= EDM_MAX_E) */
@@ -229,6 +235,21 @@ size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *
 int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
                         int64_t lib_begin, int64_t lib_count, const edm_params *params,
                         float *rho, int64_t ld_rho, void *stream);
+
+/* Series index found by the last EDM_FLAG_VALIDATE scan on this thread
+   that failed (first series holding a non-finite value), else -1. */
+int64_t edm_last_bad_series(void);
+
+/*
+ * Rare-path accounting of the kNN kernels on the current device (the
+ * certified FP32 ranking of Sec. III-B's tables falls back to FP64 where a
+ * gap between neighbour distances is within the FP32 error bound):
+ *   reranks     queries whose kept entries were re-ranked in FP64
+ *   exhaustive  queries re-solved by an exhaustive FP64 scan
+ * Counts accumulate over every kNN launch since the last reset (reset != 0
+ * clears them after reading).  Synchronises the device.
+ */
+int edm_knn_counters(int64_t *reranks, int64_t *exhaustive, int reset);
 
 /* Human-readable text for a status code (includes the CUDA error if any). */
 const char *edm_status_string(int status);

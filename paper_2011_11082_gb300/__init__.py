@@ -19,6 +19,7 @@ from ._abi import (
     EDM_PRECISION_FP16_TARGETS,
     EDM_PRECISION_FP32,
     EDM_FLAG_LOOKUP_SCALAR,
+    EDM_FLAG_VALIDATE,
     EdmError,
     edm_params,
 )
@@ -32,6 +33,7 @@ __all__ = [
     "edm_ccm_rho_backward",
     "edm_ccm_backward_workspace_bytes",
     "edm_ccm_rho_batched",
+    "edm_knn_counters",
     "CCMBatch",
     "ccm",
     "ccm_rho_autograd",
@@ -65,14 +67,16 @@ def _dev_f32(Y: torch.Tensor, name: str) -> torch.Tensor:
 
 
 def edm_optimal_E(Y: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, return_rho: bool = True,
-                  stream=None):
-    """Phase 1 (simplex projection): optE int32[N] and rho_by_E float32[N][E_max]."""
+                  stream=None, flags: int = 0):
+    """Phase 1 (simplex projection): optE int32[N] and rho_by_E float32[N][E_max].
+    ``flags=EDM_FLAG_VALIDATE`` first checks Y for non-finite values (the
+    error names the first bad series)."""
     lib = _abi.load()
     Y = _dev_f32(Y, "Y")
     N, T = Y.shape
     optE = torch.empty(N, dtype=torch.int32, device=Y.device)
     rho = torch.empty((N, E_max), dtype=torch.float32, device=Y.device) if return_rho else None
-    p = make_params(E_max=E_max, tau=tau, Tp=Tp)
+    p = make_params(E_max=E_max, tau=tau, Tp=Tp, flags=flags)
     st = lib.edm_optimal_E(Y.data_ptr(), N, T, _ld(Y), ctypes.byref(p), optE.data_ptr(),
                            rho.data_ptr() if rho is not None else None, _stream(stream))
     _abi.check(st, "edm_optimal_E")
@@ -95,6 +99,15 @@ def edm_knn_table(Y: torch.Tensor, E: int, tau: int = 1, Tp: int = 1, exclusion_
                            _stream(stream))
     _abi.check(st, "edm_knn_table")
     return idx, w
+
+
+def edm_knn_counters(reset: bool = True) -> tuple[int, int]:
+    """(queries re-ranked in FP64, queries re-solved by an exhaustive FP64
+    scan) by the kNN kernels since the last reset (synchronises)."""
+    lib = _abi.load()
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _abi.check(lib.edm_knn_counters(ctypes.byref(a), ctypes.byref(b), 1 if reset else 0), "edm_knn_counters")
+    return int(a.value), int(b.value)
 
 
 def edm_ccm_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,

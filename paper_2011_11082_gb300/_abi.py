@@ -19,6 +19,7 @@ EDM_MAX_T = 65535
 EDM_PRECISION_FP32 = 0
 EDM_PRECISION_FP16_TARGETS = 1
 EDM_FLAG_LOOKUP_SCALAR = 1
+EDM_FLAG_VALIDATE = 2
 
 
 class edm_params(ctypes.Structure):
@@ -64,6 +65,8 @@ SIGNATURES = {
     "edm_ccm_rho_batched": (ctypes.c_int, [ctypes.POINTER(edm_dataset), _i32, _pp, _vp, ctypes.c_size_t, _vp]),
     "edm_ccm_rho_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(edm_dataset), _i32, _pp]),
     "edm_ccm_rho_batched_reset": (ctypes.c_int, []),
+    "edm_last_bad_series": (ctypes.c_int64, []),
+    "edm_knn_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "edm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "edm_last_cuda_error": (ctypes.c_int, []),
     "edm_version": (ctypes.c_int, []),
@@ -121,4 +124,8 @@ def load(build_if_missing: bool = True):
 def check(status: int, where: str):
     if status != EDM_OK:
         lib = load()
-        raise EdmError(status, where, lib.edm_status_string(status).decode())
+        msg = lib.edm_status_string(status).decode()
+        bad = int(lib.edm_last_bad_series())
+        if status == EDM_ERR_INVALID and bad >= 0:
+            msg += f" (series {bad} holds a non-finite value)"
+        raise EdmError(status, where, msg)

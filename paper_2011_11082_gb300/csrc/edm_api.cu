@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "launchers.h"
@@ -63,8 +64,29 @@ struct LaunchScope {
     }
 };
 
+thread_local int64_t g_bad_series = -1;
+
+// EDM_FLAG_VALIDATE: returns EDM_OK, or EDM_ERR_INVALID with the first bad
+// series recorded, or EDM_ERR_CUDA.
+int validate_series(const float *Y, int64_t N, int64_t T, int64_t ldY, const edm_params *p, cudaStream_t st)
+{
+    g_bad_series = -1;
+    if (!(p->flags & EDM_FLAG_VALIDATE))
+        return EDM_OK;
+    int64_t bad = -1;
+    cudaError_t e = edm::first_nonfinite_series(Y, N, T, ldY, st, &bad);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (bad >= 0) {
+        g_bad_series = bad;
+        return EDM_ERR_INVALID;
+    }
+    return EDM_OK;
+}
+
 int check_common(const edm_params *p)
 {
+    g_bad_series = -1;
     if (!p)
         return EDM_ERR_INVALID;
     if (p->tau < 1 || p->Tp < 0 || p->exclusion_radius < -1)
@@ -162,6 +184,41 @@ CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
 }  // namespace
 
 namespace edm {
+
+static __device__ unsigned long long g_first_bad;
+
+__global__ void nonfinite_kernel(const float *__restrict__ Y, int64_t N, int64_t T, int64_t ldY)
+{
+    for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
+        bool bad = false;
+        for (int64_t t = threadIdx.x; t < T; t += blockDim.x)
+            bad |= !isfinite(Y[i * ldY + t]);
+        if (__syncthreads_or(bad) && threadIdx.x == 0)
+            atomicMin(&g_first_bad, (unsigned long long)i);
+    }
+}
+
+cudaError_t first_nonfinite_series(const float *Y, int64_t N, int64_t T, int64_t ldY, cudaStream_t st,
+                                   int64_t *first_bad)
+{
+    static std::mutex mu;  // one scan at a time uses the device word
+    std::lock_guard<std::mutex> lock(mu);
+    const unsigned long long none = ~0ull;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_first_bad, &none, sizeof none, 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return e;
+    nonfinite_kernel<<<(unsigned)std::min<int64_t>(N, 4096), 256, 0, st>>>(Y, N, T, ldY);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    unsigned long long r = none;
+    if ((e = cudaMemcpyFromSymbolAsync(&r, g_first_bad, sizeof r, 0, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return e;
+    *first_bad = r == none ? -1 : (int64_t)r;
+    return cudaSuccess;
+}
+
 void note_launches(int kernel, int64_t n) { g_launches[kernel] += n; }
 bool profiling() { return g_prof; }
 void prof_push(int kernel, cudaEvent_t a, cudaEvent_t b, double units)
@@ -221,6 +278,21 @@ int edm_profile_read(int kernel, double *ms, int64_t *launches, double *units)
 
 int edm_last_cuda_error(void) { return g_last_cuda; }
 
+int64_t edm_last_bad_series(void) { return g_bad_series; }
+
+int edm_knn_counters(int64_t *reranks, int64_t *exhaustive, int reset)
+{
+    unsigned long long c[2] = {0ull, 0ull};
+    cudaError_t e = edm::knn_counters(c, reset != 0);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (reranks)
+        *reranks = (int64_t)c[0];
+    if (exhaustive)
+        *exhaustive = (int64_t)c[1];
+    return EDM_OK;
+}
+
 const char *edm_status_string(int status)
 {
     switch (status) {
@@ -252,6 +324,8 @@ int edm_optimal_E(const float *Y, int64_t N, int64_t T, int64_t ldY, const edm_p
         return EDM_ERR_INVALID;
     if (T > edm::knn_max_T())
         return EDM_ERR_UNSUPPORTED;
+    if ((rc = validate_series(Y, N, T, ldY, params, (cudaStream_t)stream)) != EDM_OK)
+        return rc;
     {
         LaunchScope ls(EDM_KERNEL_SIMPLEX, (cudaStream_t)stream, (double)N);
         EDM_CUDA(edm::launch_simplex(Y, N, (int)T, ldY, params->E_max, params->tau, params->Tp, optE, rho_by_E,
@@ -482,6 +556,8 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
         return EDM_ERR_INVALID;
     if (ws_bytes < ccm_ws_layout(N, T, params).total)
         return EDM_ERR_WORKSPACE;
+    if ((rc = validate_series(Y, N, T, ldY, params, (cudaStream_t)stream)) != EDM_OK)
+        return rc;
     if (lib_count == 0)
         return EDM_OK;
     cudaStream_t st = (cudaStream_t)stream;

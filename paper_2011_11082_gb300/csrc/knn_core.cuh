@@ -32,6 +32,10 @@
 
 namespace edm {
 
+// Queries that needed the FP64 re-rank ([0]) and the exhaustive FP64 scan
+// ([1]) since the last read (edm_knn_counters); rare-path accounting only.
+static __device__ unsigned long long g_knn_counts[2];
+
 // list capacity for E is E + 2 + kGuard (= K + 1)
 __host__ __device__ constexpr int list_off(int E) { return (E - 1) * E / 2 + (E - 1) * (2 + kGuard); }
 constexpr int kListTotal = list_off(EDM_MAX_E + 1);
@@ -103,9 +107,26 @@ __device__ __forceinline__ float dist32(const KnnQuery &q, int s, int E)
     return d;
 }
 
-// K-th smallest of the 32 lane minima (every lane minimum is a real candidate).
+// K-th smallest of the 32 lane minima (every lane minimum is a real
+// candidate).  Small K: K rounds of a warp minimum on the (order-preserving)
+// bit patterns of the non-negative distances; large K: a bitonic sort.
 __device__ __forceinline__ float kth_lane_min(float mn, int K)
 {
+    if (K <= 12) {
+        unsigned v = __float_as_uint(mn);
+        unsigned m = 0u;
+        int got = 0;
+        while (got < K) {  // warp-uniform
+            m = __reduce_min_sync(kFull, v);
+            const unsigned hit = __ballot_sync(kFull, v == m);
+            got += __popc(hit);
+            if (v == m)
+                v = 0xffffffffu;
+            if (m == 0x7f800000u)  // +inf: fewer than K finite lane minima
+                break;
+        }
+        return __uint_as_float(m);
+    }
     float srt = warp_sort_asc(mn);
     return __shfl_sync(kFull, srt, K - 1);
 }
@@ -433,12 +454,16 @@ __device__ __noinline__ void finalize_E(const KnnQuery q, KnnWarpScratch &sc, in
         exhaustive64(q, sc, E, k);
         use64 = true;
     }
+    if (use64 && lane == 0)
+        atomicAdd(&g_knn_counts[full ? 1 : 0], 1ull);
 
     int s_n = 0;
     float w = 0.f;
     if (use64) {
         double dd = lane < k ? sqrt(sc.l64[lane]) : 0.0;
-        s_n = lane < k ? sc.ls64[lane] : 0;
+        // (an exhaustive scan over non-finite distances finds no candidate
+        // and leaves a sentinel; keep every emitted index inside the series)
+        s_n = lane < k ? min(max(sc.ls64[lane], q.s_first), q.s_last) : 0;
         double d1 = __shfl_sync(kFull, dd, 0);
         double u = 0.0;
         if (lane < k)
@@ -456,22 +481,64 @@ __device__ __noinline__ void finalize_E(const KnnQuery q, KnnWarpScratch &sc, in
     emit(E, k, s_n, w, lane < k);
 }
 
+// Minimum of a lane's slots as a balanced tree (no serial dependency chain).
+template <int J>
+__device__ __forceinline__ float lane_min_tree(const float (&d2)[J])
+{
+    float m[J / 2];
+#pragma unroll
+    for (int j = 0; j < J / 2; ++j)
+        m[j] = fminf(d2[2 * j], d2[2 * j + 1]);
+#pragma unroll
+    for (int w = J / 2; w > 1; w = (w + 1) / 2) {
+#pragma unroll
+        for (int j = 0; j < w / 2; ++j)
+            m[j] = fminf(m[2 * j], m[2 * j + 1]);
+        if (w & 1)
+            m[w / 2] = m[w - 1];
+    }
+    return m[0];
+}
+
+// Bit j of (m0, m1) = slot j has d2 <= th; the bits of each 8-slot group are
+// formed independently and then merged (short dependency chains).
+template <int J>
+__device__ __forceinline__ void mark_le(const float (&d2)[J], float th, unsigned &m0, unsigned &m1)
+{
+    unsigned g[(J + 7) / 8];
+#pragma unroll
+    for (int b = 0; b < (J + 7) / 8; ++b) {
+        unsigned v = 0u;
+#pragma unroll
+        for (int u = 0; u < 8 && 8 * b + u < J; ++u)
+            v |= (d2[8 * b + u] <= th ? 1u : 0u) << u;
+        g[b] = v;
+    }
+    m0 = 0u;
+    m1 = 0u;
+#pragma unroll
+    for (int b = 0; b < (J + 7) / 8; ++b) {
+        if (b < 4)
+            m0 |= g[b] << (8 * b);
+        else
+            m1 |= g[b] << (8 * (b - 4));
+    }
+}
+
 // Candidates of the warp with d2 <= th (registers only).
 template <int J>
 __device__ __forceinline__ int count_le(const float (&d2)[J], float th)
 {
-    int n = 0;
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-        n += d2[j] <= th ? 1 : 0;
-    return __reduce_add_sync(kFull, (unsigned)n);
+    unsigned m0, m1;
+    mark_le(d2, th, m0, m1);
+    return (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
 }
 
 // Selection of one chunk for E (inline: the distance registers stay live
 // across it).  1) A threshold that at least K = E+3 real candidates meet:
 // the smaller of the grown previous list and the K-th smallest lane
-// minimum.  2) If more than the buffer holds are at or below it, tighten it
-// by counting rounds on the registers (the count of points within squared
+// minimum.  2) If more than 32 are at or below it, tighten it by counting
+// rounds on the registers (the count of points within squared
 // radius th grows about linearly for points near a low-dimensional
 // attractor), keeping the count >= K.  3) Store
 // the distances to the warp scratch, compact the marked candidates behind
@@ -485,20 +552,21 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
     const int K = E + 1 + kGuard;
     const int lo_l = list_off(E);
     const int have = sc.lcount[E];
-    float mn = CUDART_INF_F;
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-        mn = fminf(mn, d2[j]);
+    const float mn = lane_min_tree(d2);
     float th = fminf(seed_threshold(q, sc, E, prevE), kth_lane_min(mn, K));
     th = fminf(th, 3.40282347e38f);  // never mark a +inf slot (not a candidate)
-    int c = have + count_le(d2, th);
-    if (c > kCandCap) {
+    unsigned m0, m1;
+    mark_le(d2, th, m0, m1);
+    int c = have + (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
+    if (c > 32) {
+        // aim for <= 32 buffered entries: the rank-select then keeps one
+        // entry per lane (shuffles only)
         // counting rounds; invariant: at least K real candidates (list
         // entries of earlier chunks or this chunk's slots) are <= hi
         float hi = th, lo = 0.f;
         int c_hi = c - have;
         const float want = (float)(K + 8);
-        for (int r = 0; r < 8 && have + c_hi > kCandCap; ++r) {
+        for (int r = 0; r < 8 && have + c_hi > 32; ++r) {
             // the embedded points lie near a low-dimensional attractor, so
             // the count grows about linearly in th (not like th^(E/2))
             float g = lo > 0.f ? sqrtf(lo * hi) : hi * (want / (float)c_hi);
@@ -515,22 +583,13 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
         }
         th = hi;
         c = have + c_hi;
+        mark_le(d2, th, m0, m1);
     }
     // distances of this E to the scratch (16-byte stores, conflict-free)
 #pragma unroll
     for (int j4 = 0; j4 < J / 4; ++j4)
         reinterpret_cast<float4 *>(q.d2s)[j4 * 32 + lane] =
             make_float4(d2[4 * j4], d2[4 * j4 + 1], d2[4 * j4 + 2], d2[4 * j4 + 3]);
-    unsigned m0 = 0u, m1 = 0u;
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        if (d2[j] <= th) {
-            if (j < 32)
-                m0 |= 1u << j;
-            else
-                m1 |= 1u << (j - 32);
-        }
-    }
     __syncwarp();
     if (c <= kCandCap) {
         int total;

@@ -390,4 +390,14 @@ cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int
     return knn_dispatch<true>(Y, ldY, 0, n_lib, T, tau, Tp, excl, 1u << (E - 1), lay, nullptr, idx, w, E, st);
 }
 
+cudaError_t knn_counters(unsigned long long out[2], bool reset)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_knn_counts, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess && reset) {
+        const unsigned long long z[2] = {0ull, 0ull};
+        e = cudaMemcpyToSymbol(g_knn_counts, z, sizeof z);
+    }
+    return e;
+}
+
 }  // namespace edm

@@ -34,6 +34,10 @@ cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_l
                               uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
                               int q_per_cta = 64, const uint32_t *sel_dev = nullptr);
 
+// FP64 re-rank / exhaustive-scan query counts of the kNN kernels on the
+// current device (synchronises); reset clears them.
+cudaError_t knn_counters(unsigned long long out[2], bool reset);
+
 // Public table format: idx int32 [n_lib][Tq][E+1] (unshifted), w float [n_lib][Tq][E+1].
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
                               int32_t *idx, float *w, cudaStream_t st);
@@ -84,6 +88,11 @@ cudaError_t launch_lookup_multi(const LookupArgs &a, int RB, cudaStream_t st);
 cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
                                     const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st,
                                     int RB = 128);
+
+// Validation pass (EDM_FLAG_VALIDATE): index of the first series holding a
+// non-finite value, or -1 (synchronises `st`).
+cudaError_t first_nonfinite_series(const float *Y, int64_t N, int64_t T, int64_t ldY, cudaStream_t st,
+                                   int64_t *first_bad);
 
 // Launch accounting shared by the translation units (edm_api.cu).
 void note_launches(int kernel, int64_t n);

@@ -11,8 +11,9 @@
 // address operation per 4 (FP32) or 8 (FP16) target values.  Accumulation
 // is FP32 (Algorithm 5's weighted sum; then the rho moment sums).  The FP16
 // form feeds the FP16 values straight into mixed-precision FMAs (FP16
-// operands, exact FP32 product, FP32 accumulator) with each weight split
-// into two FP16 halves w = hi + lo, so no separate conversion is issued.
+// operands, exact FP32 product, FP32 accumulator) with an FP16 copy of each
+// weight (the tables stay FP32), so no separate conversion is issued: one
+// FMA per gathered value, as in the FP32 form, at half the shared bytes.
 #pragma once
 
 #include "edm_internal.cuh"
@@ -53,14 +54,8 @@ __device__ __forceinline__ void fma_h2(float &pl, float &ph, uint32_t u, uint16_
         : "r"(u), "h"(w));
 }
 
-// w = hi + lo with both halves in FP16 (relative error of hi + lo <= 2^-22).
-__device__ __forceinline__ void split_w(float w, uint16_t &hi, uint16_t &lo)
-{
-    const __half h = __float2half_rn(w);
-    const __half l = __float2half_rn(w - __half2float(h));
-    hi = __half_as_ushort(h);
-    lo = __half_as_ushort(l);
-}
+// FP16 copy of a weight (round to nearest) as an FMA operand.
+__device__ __forceinline__ uint16_t w_f16(float w) { return __half_as_ushort(__float2half_rn(w)); }
 
 // Chunk position a lane starts from: with 128-byte rows the eight lanes of
 // a quarter-warp take positions 0..7; with 64-byte rows lanes pair up
@@ -190,11 +185,11 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
                 }
                 const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
                 const uint32_t Bo = base + orow * (uint32_t)RB + lane16;
-                uint16_t whi[F16 ? K : 1], wlo[F16 ? K : 1];
+                uint16_t wh[F16 ? K : 1];
                 if (F16) {
 #pragma unroll
                     for (int n = 0; n < (F16 ? K : 1); ++n)
-                        split_w(wn[n], whi[n], wlo[n]);
+                        wh[n] = w_f16(wn[n]);
                 }
 #pragma unroll
                 for (int cl = 0; cl < CPP; ++cl) {
@@ -227,8 +222,7 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
                             const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
-                                fma_h2(pl[i], ph[i], uu[i], whi[n]);
-                                fma_h2(pl[i], ph[i], uu[i], wlo[n]);
+                                fma_h2(pl[i], ph[i], uu[i], wh[n]);
                             }
                         }
                         const uint4 ou = lds_u4(Bo ^ x);

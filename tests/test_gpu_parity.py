@@ -229,3 +229,54 @@ def test_ccm_long_series_narrow_tiles(edm):
     assert np.abs(got - R).max() < RHO_TOL
     got16 = edm.edm_ccm_rho(Yd, Ed, precision=edm.EDM_PRECISION_FP16_TARGETS).t().cpu().numpy()
     assert np.abs(got16 - R).max() < FP16_TOL
+
+
+def test_validation_flag_names_first_bad_series(edm):
+    """EDM_FLAG_VALIDATE: a non-finite value is reported (first bad series)
+    before any compute kernel runs; clean data gives the unvalidated results."""
+    from paper_2011_11082_gb300 import _abi
+
+    lib = _abi.load()
+    Y = synth.coupled_logistic(12, 300, 0.05, 0.05, seed_data=61, seed_noise=62)
+    clean = _dev(Y)
+    bad = Y.copy()
+    bad[9, 3] = np.inf
+    bad[7, 120] = np.nan
+    Yb = _dev(bad)
+    with pytest.raises(edm.EdmError) as ei:
+        edm.edm_optimal_E(Yb, E_max=6, flags=edm.EDM_FLAG_VALIDATE)
+    assert ei.value.status == 1 and "series 7" in str(ei.value)
+    assert lib.edm_last_bad_series() == 7
+    optE = torch.full((12,), 2, dtype=torch.int32, device="cuda")
+    with pytest.raises(edm.EdmError):
+        edm.edm_ccm_rho(Yb, optE, flags=edm.EDM_FLAG_VALIDATE)
+    assert lib.edm_last_bad_series() == 7
+    a, _ = edm.edm_optimal_E(clean, E_max=6, flags=edm.EDM_FLAG_VALIDATE)
+    assert lib.edm_last_bad_series() == -1
+    b, _ = edm.edm_optimal_E(clean, E_max=6)
+    assert torch.equal(a, b)
+    r1 = edm.edm_ccm_rho(clean, a, flags=edm.EDM_FLAG_VALIDATE)
+    r2 = edm.edm_ccm_rho(clean, a)
+    assert torch.equal(r1, r2)
+
+
+def test_knn_fp64_fallback_counts(edm):
+    """The certified FP32 ranking falls back to FP64 only near ties: on the
+    coupled maps the re-rank share is reported and small; exact duplicates
+    (an integer-period sine) always take the FP64 path."""
+    Y = synth.workload("n64_t500")
+    Yd = _dev(Y)
+    edm.edm_knn_counters(reset=True)
+    oE, _ = edm.edm_optimal_E(Yd, E_max=10, return_rho=False)
+    edm.edm_ccm_rho(Yd, oE)
+    torch.cuda.synchronize()
+    rr, ex = edm.edm_knn_counters(reset=True)
+    n_E = len(set(oE.cpu().numpy().tolist()))
+    queries = 64 * 250 * 10 + 64 * 500 * n_E  # phase 1 (all E) + phase 2 tables (upper bound)
+    print(f"n64_t500: FP64 re-ranks {rr}, exhaustive {ex}, of about {queries} (query, E) selections")
+    assert rr + ex <= 0.01 * queries
+    sine = np.stack([synth.sine_series(240, 12.0), synth.sine_series(240, 12.0, phase=0.3)])
+    edm.edm_knn_table(_dev(sine), 3)
+    torch.cuda.synchronize()
+    rr2, ex2 = edm.edm_knn_counters(reset=True)
+    assert rr2 + ex2 > 0
