@@ -395,22 +395,78 @@ __device__ __noinline__ void exhaustive64(const KnnQuery q, KnnWarpScratch &sc, 
     __syncwarp();
 }
 
-// Final neighbours of (query, E) with exact order; lanes n < k receive
-// (s_n, w_n) and call emit(E, k, s_n, w_n, lane < k).
-template <class Emit>
-__device__ __noinline__ void finalize_E(const KnnQuery q, KnnWarpScratch &sc, int E, Emit &emit)
+// Rare path of the finalisation: FP64 re-rank of the kept entries (and an
+// exhaustive FP64 scan when even the guard entries cannot separate the k-th
+// place from the entries left out), FP64 weights.  Lanes n < k receive
+// (s_n, w_n).
+__device__ __noinline__ void finalize64(const KnnQuery q, KnnWarpScratch &sc, int E, bool full, int &s_out,
+                                        float &w_out)
 {
     const int lane = lane_id();
     const int k = E + 1;
     const int lo = list_off(E);
     const int K = E + 1 + kGuard;
     const int have = min(sc.lcount[E], K);
-
-    bool use64 = false;
-    bool full = sc.ovf[E] != 0 || have < k;
     if (!full) {
-        float Dn = lane < have ? sc.ld[lo + lane] : CUDART_INF_F;
-        float Dn1 = __shfl_down_sync(kFull, Dn, 1);
+        double d64 = CUDART_INF;
+        int s_me = 0;
+        if (lane < have) {
+            s_me = sc.ls[lo + lane];
+            d64 = dist64(q.xq, q.t, q.xc, s_me, E, q.tau);
+        }
+        int r = 0;
+        for (int f = 0; f < have; ++f) {
+            double df = __shfl_sync(kFull, d64, f);
+            int sf = __shfl_sync(kFull, s_me, f);
+            r += (df < d64) || (df == d64 && sf < s_me);
+        }
+        if (lane < have) {
+            sc.l64[r] = d64;
+            sc.ls64[r] = s_me;
+        }
+        __syncwarp();
+        // entries left out have FP32 distance >= the last kept one
+        if (have >= K) {
+            float Dlast = sc.ld[lo + have - 1];
+            full = !(sc.l64[k - 1] < (double)(Dlast - d2_err(Dlast, E)));
+        }
+    }
+    if (full)
+        exhaustive64(q, sc, E, k);
+    if (lane == 0)
+        atomicAdd(&g_knn_counts[full ? 1 : 0], 1ull);
+    double dd = lane < k ? sqrt(sc.l64[lane]) : 0.0;
+    // (an exhaustive scan over non-finite distances finds no candidate and
+    // leaves a sentinel; keep every emitted index inside the series)
+    s_out = lane < k ? min(max(sc.ls64[lane], q.s_first), q.s_last) : 0;
+    double d1 = __shfl_sync(kFull, dd, 0);
+    double u = 0.0;
+    if (lane < k)
+        u = d1 > 0.0 ? exp(-dd / d1) : (dd == 0.0 ? 1.0 : 0.0);
+    double sum = warp_sum_d(u);
+    w_out = (float)(u / sum);
+}
+
+// Final neighbours of (query, E) with exact order; lanes n < k receive
+// (s_n, w_n) and call emit(E, k, s_n, w_n, lane < k).  Common path inline:
+// the FP32 order is certified (every gap among the first E+2 entries
+// exceeds the summed error bounds, no near duplicate) and the weights are
+// FP32; everything else goes to finalize64.
+template <class Emit>
+__device__ __forceinline__ void finalize_E(const KnnQuery &q, KnnWarpScratch &sc, int E, Emit &emit)
+{
+    const int lane = lane_id();
+    const int k = E + 1;
+    const int lo = list_off(E);
+    const int K = E + 1 + kGuard;
+    const int have = min(sc.lcount[E], K);
+    const bool full = sc.ovf[E] != 0 || have < k;
+    bool all_ok = false;
+    float Dn = 0.f, D0 = 0.f;
+    if (!full) {
+        Dn = lane < have ? sc.ld[lo + lane] : CUDART_INF_F;
+        const float Dn1 = lane + 1 < have ? sc.ld[lo + lane + 1] : CUDART_INF_F;
+        D0 = sc.ld[lo];
         bool ok = true;
         if (lane < k) {
             if (lane + 1 < have)
@@ -418,65 +474,18 @@ __device__ __noinline__ void finalize_E(const KnnQuery q, KnnWarpScratch &sc, in
             else
                 ok = have < K;  // nothing was left out beyond the list
         }
-        float D0 = __shfl_sync(kFull, Dn, 0);
-        bool all_ok = __all_sync(kFull, ok) && D0 >= kNearDup;
-        if (!all_ok) {
-            // FP64 re-rank of the kept entries.
-            double d64 = CUDART_INF;
-            int s_me = 0;
-            if (lane < have) {
-                s_me = sc.ls[lo + lane];
-                d64 = dist64(q.xq, q.t, q.xc, s_me, E, q.tau);
-            }
-            int r = 0;
-            for (int f = 0; f < have; ++f) {
-                double df = __shfl_sync(kFull, d64, f);
-                int sf = __shfl_sync(kFull, s_me, f);
-                r += (df < d64) || (df == d64 && sf < s_me);
-            }
-            if (lane < have) {
-                sc.l64[r] = d64;
-                sc.ls64[r] = s_me;
-            }
-            __syncwarp();
-            // entries left out have FP32 distance >= the last kept one
-            bool bound_ok = true;
-            if (have >= K) {
-                float Dlast = sc.ld[lo + have - 1];
-                bound_ok = sc.l64[k - 1] < (double)(Dlast - d2_err(Dlast, E));
-            }
-            if (!bound_ok)
-                full = true;
-            use64 = true;
-        }
+        all_ok = __all_sync(kFull, ok) && D0 >= kNearDup;
     }
-    if (full) {
-        exhaustive64(q, sc, E, k);
-        use64 = true;
-    }
-    if (use64 && lane == 0)
-        atomicAdd(&g_knn_counts[full ? 1 : 0], 1ull);
-
     int s_n = 0;
     float w = 0.f;
-    if (use64) {
-        double dd = lane < k ? sqrt(sc.l64[lane]) : 0.0;
-        // (an exhaustive scan over non-finite distances finds no candidate
-        // and leaves a sentinel; keep every emitted index inside the series)
-        s_n = lane < k ? min(max(sc.ls64[lane], q.s_first), q.s_last) : 0;
-        double d1 = __shfl_sync(kFull, dd, 0);
-        double u = 0.0;
-        if (lane < k)
-            u = d1 > 0.0 ? exp(-dd / d1) : (dd == 0.0 ? 1.0 : 0.0);
-        double sum = warp_sum_d(u);
-        w = (float)(u / sum);
-    } else {
-        float dd = lane < k ? sqrtf(sc.ld[lo + lane]) : 0.f;
+    if (all_ok) {
+        const float dd = lane < k ? sqrtf(Dn) : 0.f;
         s_n = lane < k ? sc.ls[lo + lane] : 0;
-        float d1 = __shfl_sync(kFull, dd, 0);
-        float u = lane < k ? expf(-dd / d1) : 0.f;
-        float sum = warp_sum(u);
-        w = u / sum;
+        const float inv_d1 = __frcp_rn(sqrtf(D0));
+        const float u = lane < k ? expf(-dd * inv_d1) : 0.f;
+        w = u * __frcp_rn(warp_sum(u));
+    } else {
+        finalize64(q, sc, E, full, s_n, w);
     }
     emit(E, k, s_n, w, lane < k);
 }
@@ -536,9 +545,10 @@ __device__ __forceinline__ int count_le(const float (&d2)[J], float th)
 
 // Selection of one chunk for E (inline: the distance registers stay live
 // across it).  1) A threshold that at least K = E+3 real candidates meet:
-// the smaller of the grown previous list and the K-th smallest lane
-// minimum.  2) If more than 32 are at or below it, tighten it by counting
-// rounds on the registers (the count of points within squared
+// the grown previous list (or this E's list of earlier chunks) when that
+// alone marks at most a buffer's worth, else its minimum with the K-th
+// smallest lane minimum.  2) If more than the buffer holds are at or below it, tighten it
+// by counting rounds on the registers (the count of points within squared
 // radius th grows about linearly for points near a low-dimensional
 // attractor), keeping the count >= K.  3) Store
 // the distances to the warp scratch, compact the marked candidates behind
@@ -552,21 +562,26 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
     const int K = E + 1 + kGuard;
     const int lo_l = list_off(E);
     const int have = sc.lcount[E];
-    const float mn = lane_min_tree(d2);
-    float th = fminf(seed_threshold(q, sc, E, prevE), kth_lane_min(mn, K));
-    th = fminf(th, 3.40282347e38f);  // never mark a +inf slot (not a candidate)
-    unsigned m0, m1;
-    mark_le(d2, th, m0, m1);
-    int c = have + (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
-    if (c > 32) {
-        // aim for <= 32 buffered entries: the rank-select then keeps one
-        // entry per lane (shuffles only)
+    // never mark a +inf slot (not a candidate): thresholds are clamped
+    float th = fminf(seed_threshold(q, sc, E, prevE), 3.40282347e38f);
+    unsigned m0 = 0u, m1 = 0u;
+    int c = kCandCap + 1;
+    if (th < 3.40282347e38f) {  // a seed exists: often tight enough alone
+        mark_le(d2, th, m0, m1);
+        c = have + (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
+    }
+    if (c > kCandCap) {
+        th = fminf(th, fminf(kth_lane_min(lane_min_tree(d2), K), 3.40282347e38f));
+        mark_le(d2, th, m0, m1);
+        c = have + (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
+    }
+    if (c > kCandCap) {
         // counting rounds; invariant: at least K real candidates (list
         // entries of earlier chunks or this chunk's slots) are <= hi
         float hi = th, lo = 0.f;
         int c_hi = c - have;
         const float want = (float)(K + 8);
-        for (int r = 0; r < 8 && have + c_hi > 32; ++r) {
+        for (int r = 0; r < 8 && have + c_hi > kCandCap; ++r) {
             // the embedded points lie near a low-dimensional attractor, so
             // the count grows about linearly in th (not like th^(E/2))
             float g = lo > 0.f ? sqrtf(lo * hi) : hi * (want / (float)c_hi);

@@ -54,6 +54,39 @@ __device__ __forceinline__ void fma_h2(float &pl, float &ph, uint32_t u, uint16_
         : "r"(u), "h"(w));
 }
 
+// Packed FP32 pairs (two IEEE single operations per instruction; each lane
+// of the pair rounds exactly like the scalar operation).
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void unpk2(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+
+// (p0, p1) += w * (v0, v1)
+__device__ __forceinline__ void fma2(unsigned long long &p, unsigned long long ww, unsigned long long v)
+{
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(p) : "l"(ww), "l"(v));
+}
+
+// Pearson moment sums of two slots: S_p += p, S_pp += p*p, S_po += p*o.
+__device__ __forceinline__ void mom2(float &sp0, float &sp1, float &spp0, float &spp1, float &spo0, float &spo1,
+                                     float p0, float p1, float o0, float o1)
+{
+    asm("{\n\t.reg .b64 P, O, A;\n\t"
+        "mov.b64 P, {%6, %7};\n\tmov.b64 O, {%8, %9};\n\t"
+        "mov.b64 A, {%0, %1};\n\tadd.rn.f32x2 A, A, P;\n\tmov.b64 {%0, %1}, A;\n\t"
+        "mov.b64 A, {%2, %3};\n\tfma.rn.f32x2 A, P, P, A;\n\tmov.b64 {%2, %3}, A;\n\t"
+        "mov.b64 A, {%4, %5};\n\tfma.rn.f32x2 A, P, O, A;\n\tmov.b64 {%4, %5}, A;\n\t}"
+        : "+f"(sp0), "+f"(sp1), "+f"(spp0), "+f"(spp1), "+f"(spo0), "+f"(spo1)
+        : "f"(p0), "f"(p1), "f"(o0), "f"(o1));
+}
+
 // FP16 copy of a weight (round to nearest) as an FMA operand.
 __device__ __forceinline__ uint16_t w_f16(float w) { return __half_as_ushort(__float2half_rn(w)); }
 
@@ -96,6 +129,7 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
     constexpr int SET = CR * 4;                    // targets per set (lo / hi)
     constexpr int HS = CPP * 4;                    // first hi slot (FP16)
     constexpr bool kPref = K <= 16;
+    constexpr bool kPref2 = F16 && K <= 5;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
     const uint32_t pad = (128u - (raw & 127u)) & 127u;
@@ -148,14 +182,24 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
                 Spp[r] = 0.f;
                 Spo[r] = 0.f;
             }
-            float wq[kPref ? K : 1];
-            uint32_t iq[kPref ? K : 1];
+            // table entries prefetched one row block ahead (two for FP16
+            // with small K: its row blocks are half as long)
+            float wq[kPref ? K : 1], wq2[kPref2 ? K : 1];
+            uint32_t iq[kPref ? K : 1], iq2[kPref2 ? K : 1];
             if (kPref) {
                 const bool v = lane < Tq;
 #pragma unroll
                 for (int n = 0; n < (kPref ? K : 1); ++n) {
                     wq[n] = v ? __ldg(Wt + n * tq_pad + lane) : 0.f;
                     iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane) : 0u;
+                }
+            }
+            if (kPref2) {
+                const bool v = lane + 32 < Tq;
+#pragma unroll
+                for (int n = 0; n < (kPref2 ? K : 1); ++n) {
+                    wq2[n] = v ? __ldg(Wt + n * tq_pad + lane + 32) : 0.f;
+                    iq2[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane + 32) : 0u;
                 }
             }
             for (int b = 0; b < nblk; ++b) {
@@ -169,12 +213,24 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
                         wn[n] = wq[n];
                         Bn[n] = base + iq[n] * (uint32_t)RB + lane16;
                     }
-                    const int nrow = row + 32;
-                    const bool v = nrow < Tq;
+                    if (kPref2) {
+                        const int nrow = row + 64;
+                        const bool v = nrow < Tq;
 #pragma unroll
-                    for (int n = 0; n < (kPref ? K : 1); ++n) {
-                        wq[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
-                        iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
+                        for (int n = 0; n < (kPref2 ? K : 1); ++n) {
+                            wq[n] = wq2[n];
+                            iq[n] = iq2[n];
+                            wq2[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
+                            iq2[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
+                        }
+                    } else {
+                        const int nrow = row + 32;
+                        const bool v = nrow < Tq;
+#pragma unroll
+                        for (int n = 0; n < (kPref ? K : 1); ++n) {
+                            wq[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
+                            iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
+                        }
                     }
                 } else {
 #pragma unroll
@@ -186,34 +242,48 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
                 const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
                 const uint32_t Bo = base + orow * (uint32_t)RB + lane16;
                 uint16_t wh[F16 ? K : 1];
+                // packed weight pairs for the FP32 gathers (register budget:
+                // small K only)
+                constexpr bool kPair = !F16 && K <= 12;
+                unsigned long long ww[kPair ? K : 1];
                 if (F16) {
 #pragma unroll
                     for (int n = 0; n < (F16 ? K : 1); ++n)
                         wh[n] = w_f16(wn[n]);
+                } else if (kPair) {
+#pragma unroll
+                    for (int n = 0; n < (kPair ? K : 1); ++n)
+                        ww[n] = pk2(wn[n], wn[n]);
                 }
 #pragma unroll
                 for (int cl = 0; cl < CPP; ++cl) {
                     const uint32_t x = (uint32_t)((c0 + cl) * 16);
                     if (!F16) {
                         float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+                        if (kPair) {
+                            unsigned long long p01 = 0ull, p23 = 0ull;  // (+0.0f, +0.0f)
 #pragma unroll
-                        for (int n = 0; n < K; ++n) {
-                            const float4 v = lds_v4(Bn[n] ^ x);
-                            p0 = fmaf(wn[n], v.x, p0);
-                            p1 = fmaf(wn[n], v.y, p1);
-                            p2 = fmaf(wn[n], v.z, p2);
-                            p3 = fmaf(wn[n], v.w, p3);
+                            for (int n = 0; n < (kPair ? K : 1); ++n) {
+                                const float4 v = lds_v4(Bn[n] ^ x);
+                                fma2(p01, ww[n], pk2(v.x, v.y));
+                                fma2(p23, ww[n], pk2(v.z, v.w));
+                            }
+                            unpk2(p01, p0, p1);
+                            unpk2(p23, p2, p3);
+                        } else {
+#pragma unroll
+                            for (int n = 0; n < K; ++n) {
+                                const float4 v = lds_v4(Bn[n] ^ x);
+                                p0 = fmaf(wn[n], v.x, p0);
+                                p1 = fmaf(wn[n], v.y, p1);
+                                p2 = fmaf(wn[n], v.z, p2);
+                                p3 = fmaf(wn[n], v.w, p3);
+                            }
                         }
                         const float4 o = lds_v4(Bo ^ x);
-                        const float pp[4] = {p0, p1, p2, p3};
-                        const float oo[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int sl = cl * 4 + i;
-                            Sp[sl] += pp[i];
-                            Spp[sl] = fmaf(pp[i], pp[i], Spp[sl]);
-                            Spo[sl] = fmaf(pp[i], oo[i], Spo[sl]);
-                        }
+                        const int sl = cl * 4;
+                        mom2(Sp[sl], Sp[sl + 1], Spp[sl], Spp[sl + 1], Spo[sl], Spo[sl + 1], p0, p1, o.x, o.y);
+                        mom2(Sp[sl + 2], Sp[sl + 3], Spp[sl + 2], Spp[sl + 3], Spo[sl + 2], Spo[sl + 3], p2, p3, o.z, o.w);
                     } else {
                         float pl[4] = {0.f, 0.f, 0.f, 0.f}, ph[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
