@@ -412,6 +412,102 @@ int orc_ccm_rho_rows(const double *Y, int64_t N, int64_t T, int64_t ldY, const i
     return rc_all;
 }
 
+/*
+ * Time-delay cross mapping (the lagged cross-map skill the paper cites for
+ * its adjacency maps, Sec. II-A; not defined there -- reading): for lags
+ * lag_min..lag_max, one kNN table per library and E over the points whose
+ * every lag stays inside the series -- queries = candidates = t in
+ * [max((E-1)tau, -lag_min), T-1-max(lag_max, 0)] -- and for each lag l
+ * prediction(t) = sum_n w[t,n] * y(s_n + l), observed y(t + l),
+ * rho_l = corrcoef.  With lag_min = lag_max = Tp >= 0 this is exactly the
+ * CCM above.  rho is [n_lags][n_rows][N] (library rows x all targets).
+ */
+int orc_ccm_rho_lags(const double *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                     const int64_t *rows, int64_t n_rows, int tau, int lag_min, int lag_max, int excl,
+                     double *rho, int nthreads)
+{
+    if (N < 1 || T < 2 || ldY < T || tau < 1 || lag_max < lag_min || n_rows < 0)
+        return ORC_ERR_INVALID;
+    const int n_lags = lag_max - lag_min + 1;
+    int E_top = 0;
+    for (int64_t j = 0; j < N; ++j) {
+        if (optE[j] < 1)
+            return ORC_ERR_INVALID;
+        if (optE[j] > E_top)
+            E_top = optE[j];
+    }
+    int rc_all = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads < 1)
+        nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t r = 0; r < n_rows; ++r) {
+        const double *x = Y + rows[r] * ldY;
+        for (int E = 1; E <= E_top; ++E) {
+            int used = 0;
+            for (int64_t j = 0; j < N && !used; ++j)
+                used = optE[j] == E;
+            if (!used)
+                continue;
+            int64_t L = (int64_t)(E - 1) * tau;
+            int64_t A = L > -(int64_t)lag_min ? L : -(int64_t)lag_min;
+            int64_t B = T - 1 - (lag_max > 0 ? lag_max : 0);
+            int k = E + 1;
+            int64_t nq = B - A + 1;
+            int rc = nq > k ? ORC_OK : ORC_ERR_INVALID;
+            int64_t *idx = NULL;
+            double *w = NULL, *d2 = NULL, *pred = NULL, *obs = NULL;
+            if (rc == ORC_OK) {
+                idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nq * k));
+                w = (double *)malloc(sizeof(double) * (size_t)(nq * k));
+                d2 = (double *)malloc(sizeof(double) * (size_t)k);
+                pred = (double *)malloc(sizeof(double) * (size_t)nq);
+                obs = (double *)malloc(sizeof(double) * (size_t)nq);
+                if (!idx || !w || !d2 || !pred || !obs)
+                    rc = ORC_ERR_NOMEM;
+            }
+            for (int64_t t = A; rc == ORC_OK && t <= B; ++t) {
+                int64_t q = t - A;
+                if (knn_query(x, t, x, A, B, E, tau, 1, excl, k, idx + q * k, d2) < k)
+                    rc = ORC_ERR_INVALID;
+                else
+                    simplex_weights(d2, k, w + q * k);
+            }
+            if (rc == ORC_OK) {
+                for (int64_t j = 0; j < N; ++j) {
+                    if (optE[j] != E)
+                        continue;
+                    const double *y = Y + j * ldY;
+                    for (int l = lag_min; l <= lag_max; ++l) {
+                        for (int64_t q = 0; q < nq; ++q) {
+                            double p = 0.0;
+                            for (int n = 0; n < k; ++n)
+                                p = p + w[q * k + n] * y[idx[q * k + n] + l];
+                            pred[q] = p;
+                            obs[q] = y[A + q + l];
+                        }
+                        rho[((int64_t)(l - lag_min) * n_rows + r) * N + j] = pearson(obs, pred, nq);
+                    }
+                }
+            } else {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                rc_all = rc;
+            }
+            free(idx);
+            free(w);
+            free(d2);
+            free(pred);
+            free(obs);
+        }
+    }
+    (void)nthreads;
+    (void)n_lags;
+    return rc_all;
+}
+
 /* rho for a list of (library, target) pairs; each pair builds its own table. */
 int orc_ccm_rho_pairs(const double *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
                       const int64_t *li, const int64_t *lj, int64_t n_pairs, int tau, int Tp, int excl,

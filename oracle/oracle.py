@@ -75,6 +75,9 @@ def _declare(lib):
     lib.orc_ccm_rho_pairs.restype = _int
     lib.orc_ccm_rho_pairs.argtypes = [_dp, _i64, _i64, _i64, _i32p, _i64p, _i64p, _i64, _int, _int, _int,
                                       _dp, _int]
+    lib.orc_ccm_rho_lags.restype = _int
+    lib.orc_ccm_rho_lags.argtypes = [_dp, _i64, _i64, _i64, _i32p, _i64p, _i64, _int, _int, _int, _int, _dp,
+                                     _int]
     lib.orc_max_threads.restype = _int
     lib.orc_max_threads.argtypes = []
     return lib
@@ -222,6 +225,22 @@ def ccm_rho_pairs(Y, optE, li, lj, tau=1, Tp=1, excl=0, nthreads=None, lib=None)
                                    li.size, tau, Tp, excl, _ptr(rho, _dp), nthreads or default_threads())
     if rc:
         raise ValueError(f"orc_ccm_rho_pairs failed ({rc})")
+    return rho
+
+
+def ccm_rho_lags(Y, optE, lag_min, lag_max, rows=None, tau=1, excl=0, nthreads=None, lib=None):
+    """Time-delay cross mapping: rho[l - lag_min][r][j] = rho_l(library
+    rows[r] -> target j), one table per (library, E) over the points every
+    lag keeps inside the series."""
+    Y = _f64(np.atleast_2d(Y))
+    N, T = Y.shape
+    optE = np.ascontiguousarray(optE, dtype=np.int32)
+    rows = np.arange(N, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    rho = np.full((lag_max - lag_min + 1, rows.size, N), np.nan, np.float64)
+    rc = (lib or _load()).orc_ccm_rho_lags(_ptr(Y, _dp), N, T, T, _ptr(optE, _i32p), _ptr(rows, _i64p), rows.size,
+                                           tau, lag_min, lag_max, excl, _ptr(rho, _dp), nthreads or default_threads())
+    if rc:
+        raise ValueError(f"orc_ccm_rho_lags failed ({rc})")
     return rho
 
 

@@ -118,3 +118,27 @@ def optimal_E(x, E_max, tau=1, Tp=1):
     rhos = np.array([simplex_rho(x, E, tau, Tp) for E in range(1, E_max + 1)])
     vals = np.where(np.isnan(rhos), -np.inf, rhos)
     return int(np.argmax(vals)) + 1, rhos
+
+
+def ccm_lags_pair(x_lib, y_tgt, E, lags, tau=1, excl=0) -> np.ndarray:
+    """Time-delay cross mapping, per pair: one table over the embedded
+    points whose every lag stays inside the series (queries = candidates =
+    t in [max(L, -min(lags)), T-1-max(max(lags), 0)]), then for each lag l
+    corr(y(t+l), sum_n w y(s_n+l))."""
+    x = np.asarray(x_lib, np.float64)
+    y = np.asarray(y_tgt, np.float64)
+    T = x.size
+    L = (E - 1) * tau
+    A = max(L, -min(lags))
+    B = T - 1 - max(max(lags), 0)
+    times = np.arange(A, B + 1)
+    V = embed(x, E, tau)[A - L: B - L + 1]
+    D = distance_matrix(V, V)
+    mask = np.abs(times[:, None] - times[None, :]) > excl if excl >= 0 else None
+    idx, d2 = neighbours(D, times, E + 1, mask)
+    w = np.stack([exp_weights(r) for r in d2])
+    out = []
+    for lag in lags:
+        pred = (w * y[idx + lag]).sum(axis=1)
+        out.append(corr(y[times + lag], pred))
+    return np.array(out)

@@ -219,6 +219,39 @@ def pin_direction(lib=None):
     assert R[1, 0] > R[0, 1] + 0.05, R
 
 
+def pin_lags_brute(lib=None):
+    """Time-delay cross mapping against the per-pair brute force, negative,
+    zero and positive lags, with and without exclusion."""
+    Y = _tiny_series(15, N=3, T=44)
+    optE = np.array([2, 1, 3], np.int32)
+    for lag_min, lag_max, excl in ((-3, 2, 0), (0, 4, 1), (-2, -1, -1)):
+        R = orc.ccm_rho_lags(Y, optE, lag_min, lag_max, excl=excl, nthreads=2, lib=lib)
+        lags = list(range(lag_min, lag_max + 1))
+        for i in range(3):
+            for j in range(3):
+                b = bf.ccm_lags_pair(Y[i], Y[j], int(optE[j]), lags, excl=excl)
+                assert np.allclose(R[:, i, j], b, rtol=0, atol=1e-12, equal_nan=True), (lag_min, i, j)
+
+
+def pin_lags_reduce_to_ccm(lib=None):
+    """A single lag l = Tp >= 0 is the plain cross map with that horizon."""
+    Y = _tiny_series(16, N=4, T=60)
+    optE = np.array([2, 3, 1, 2], np.int32)
+    for Tp in (0, 1, 2):
+        R = orc.ccm_rho_lags(Y, optE, Tp, Tp, excl=0 if Tp else -1, nthreads=2, lib=lib)
+        P = orc.ccm_rho_rows(Y, optE, Tp=Tp, excl=0 if Tp else -1, nthreads=2, lib=lib)
+        assert np.array_equal(R[0], P), Tp
+
+
+def pin_lags_integer_period_sine(lib=None):
+    """Integer period: exact duplicates predict every lag exactly (rho = 1)."""
+    P = 10
+    x = synth.sine_series(8 * P + 6, P)
+    Y = np.stack([x, x])
+    R = orc.ccm_rho_lags(Y, np.array([3, 3], np.int32), -4, 4, nthreads=1, lib=lib)
+    assert np.all(np.abs(R - 1.0) < 1e-12), R
+
+
 ALL_PINS = [
     pin_hand_example,
     pin_knn_brute,
@@ -236,4 +269,7 @@ ALL_PINS = [
     pin_optE_sine,
     pin_optE_logistic,
     pin_direction,
+    pin_lags_brute,
+    pin_lags_reduce_to_ccm,
+    pin_lags_integer_period_sine,
 ]

@@ -32,6 +32,10 @@ MUTANTS = {
     "weights_use_squared_distance": ("double dn = sqrt(d2[n]);", "double dn = d2[n];"),
     "nearest_distance_wrong_row": ("double d1 = sqrt(d2[0]);", "double d1 = sqrt(d2[k - 1]);"),
     "lag_step_ignores_tau": ("xa[ta - (int64_t)m * tau] - xb[tb - (int64_t)m * tau]", "xa[ta - (int64_t)m] - xb[tb - (int64_t)m]"),
+    "lags_gather_without_lag": ("p = p + w[q * k + n] * y[idx[q * k + n] + l];", "p = p + w[q * k + n] * y[idx[q * k + n]];"),
+    "lags_observation_unshifted": ("obs[q] = y[A + q + l];", "obs[q] = y[A + q];"),
+    "lags_window_start_shifted": ("int64_t A = L > -(int64_t)lag_min ? L : -(int64_t)lag_min;",
+                                  "int64_t A = 1 + (L > -(int64_t)lag_min ? L : -(int64_t)lag_min);"),
     "table_query_window_shifted": ("int got = knn_query(x, t, x, t_lo, t_hi, E, tau, 1, excl, k, idx + r * k, d2);",
                                    "int got = knn_query(x, t, x, t_lo, t_hi - 1, E, tau, 1, excl, k, idx + r * k, d2);"),
 }
