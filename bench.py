@@ -54,6 +54,45 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# shared-memory bandwidth per SM and clock (bytes / cycle): 32 banks x 4 B
+SMEM_BYTES_PER_CLK = 128.0
+
+
+def _lookup_sources_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2011_11082_gb300", "csrc")
+    for f in ("lookup_chunked.cuh", "lookup_chunked128.cu", "lookup_chunked64.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _measured_traffic(workload, precision):
+    """DRAM bytes per lookup launch from the committed ncu summary, if it was
+    taken on the lookup sources as they are now (else None)."""
+    p = os.path.join(ROOT, "profiles", "lookup_dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(f"{workload}/{precision}")
+    if not e or e.get("sources") != _lookup_sources_hash():
+        return None
+    return float(e["bytes_per_launch"])
+
+
+def _smem_gather_bytes(hist, T, Tp, s_y, N):
+    """Shared-memory bytes the lookup must read per step: for every (library,
+    target) pair, every query row reads E+1 gathered values and one
+    observation, s_y bytes each."""
+    tot = 0.0
+    for e0, cnt in enumerate(hist):
+        E = e0 + 1
+        if cnt:
+            tot += float(cnt) * (T - Tp - (E - 1)) * (E + 2) * s_y
+    return tot * N
+
+
 def _algorithmic_bytes_per_pair(N, T, s_y):
     # rho write (4 B) + every target read once + every library read once
     # + optE, spread over the N^2 pairs.
@@ -247,6 +286,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--lookup", default="chunked", choices=["chunked", "scalar"],
                     help="phase-2 gather kernels: 16-byte chunked (default) or scalar (comparison)")
+    ap.add_argument("--knn", default="auto", choices=["auto", "warp"],
+                    help="kNN tables: thread-per-query kernel where it applies (auto) or warp-per-query only")
     ap.add_argument("--cpu-rows", type=int, default=0, help="library rows the oracle times (0: 2 x cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -281,7 +322,8 @@ def main():
     Y = edm_synth.coupled_logistic(N, T, dens, bmax, seed_data=rank, seed_noise=1 + rank)
     Yd = torch.from_numpy(Y).to(dev)
     prec = edm.EDM_PRECISION_FP16_TARGETS if args.precision == "fp16" else edm.EDM_PRECISION_FP32
-    flags = edm.EDM_FLAG_LOOKUP_SCALAR if args.lookup == "scalar" else 0
+    flags = (edm.EDM_FLAG_LOOKUP_SCALAR if args.lookup == "scalar" else 0) | \
+        (edm.EDM_FLAG_KNN_WARP if args.knn == "warp" else 0)
     rho = torch.empty((N, N), dtype=torch.float32, device=dev)
     ws = torch.empty(edm.edm_ccm_workspace_bytes(N, T, precision=prec), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -339,8 +381,20 @@ def main():
     per_launch_s = lk["ms"] / 1e3 / lk_launches
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind, "kernel": "lookup_kernel",
-                "bytes_per_pair": bpp, "path_frac": (N * float(N) * bpp / (ms / 1e3) / 1e9) / peak}
+                "traffic": _measured_traffic(args.workload, args.precision), "peak_kind": peak_kind,
+                "kernel": "lookup_kernel", "bytes_per_pair": bpp,
+                "path_frac": (N * float(N) * bpp / (ms / 1e3) / 1e9) / peak}
+    # the bound that holds: the lookup reads every gathered value from
+    # shared memory (peak = 128 B/clk/SM x SMs x the SM clock seen)
+    hist_now = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:]
+    sm_bytes = _smem_gather_bytes(hist_now, T, 1, s_y, N)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+    sm_peak = SMEM_BYTES_PER_CLK * n_sm * clk_hz / 1e12
+    sm_ach = sm_bytes / (lk["ms"] / 1e3) / 1e12 if lk["ms"] > 0 else 0.0
+    roofline_smem = {"bound": "smem", "achieved": sm_ach, "peak": sm_peak, "unit": "TB/s", "frac": sm_ach / sm_peak,
+                     "kernel": "lookup_kernel", "bytes_per_step": sm_bytes,
+                     "peak_from": f"{SMEM_BYTES_PER_CLK:.0f} B/clk/SM x {n_sm} SMs x {clk_hz / 1e6:.0f} MHz"}
 
     # end to end through the public API with host buffers: edm_ccm_host
     # copies the series in, runs both phases and streams rho back to the host
@@ -392,10 +446,10 @@ def main():
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16-targets/f32-accumulate",
             "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "T": T, "E_max": E_max, "tau": 1, "Tp": 1,
-                       "precision": args.precision, "lookup": args.lookup, "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)",
+                       "precision": args.precision, "lookup": args.lookup, "knn": args.knn, "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)",
                        "optE_histogram": hist},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "kernels": prof,
+            "roofline": roofline, "roofline_smem": roofline_smem, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches, "kernels": prof,
         }
         print(json.dumps(line), flush=True)
     if dist:

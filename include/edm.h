@@ -60,6 +60,10 @@ extern "C" {
    series holds one, return EDM_ERR_INVALID without computing and keep its
    index for edm_last_bad_series().  The scan synchronises `stream`. */
 #define EDM_FLAG_VALIDATE 2u
+/* kNN tables: always use the warp-per-query kernel (by default a table set
+   of one E <= 6 at tau = 1 uses the thread-per-query kernel; same
+   neighbours, weights equal up to the summation order) */
+#define EDM_FLAG_KNN_WARP 4u
 
 typedef struct edm_params {
     int32_t E_max;            /* phase 1 searches E = 1..E_max (<= EDM_MAX_E) */
@@ -125,6 +129,27 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
 
 /* Workspace edm_ccm_rho needs for N series of length T (bytes). */
 size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
+
+/*
+ * Time-delay cross mapping (the lagged cross-map skill the paper's adjacency
+ * maps come from, Sec. II-A; not defined there): for every lag l in
+ * lag_min..lag_max, rho_l(i, j) = corrcoef(y_j(t + l), sum_n w[t,n]
+ * y_j(s_n + l)) from ONE kNN table per library and E (E = optE[j]), built
+ * over the points whose every lag stays inside the series: queries =
+ * candidates = t in [max((E-1)tau, -lag_min), T-1-max(lag_max, 0)].  A single
+ * lag l = Tp >= 0 gives exactly edm_ccm_rho with horizon Tp.  params->Tp is
+ * ignored; all N libraries.
+ *   rho   [n_lags][N][ld_rho] target-major per lag:
+ *         rho[(l - lag_min) * N * ld_rho + j * ld_rho + i] = rho_l(i -> j)
+ *   ws    edm_ccm_rho_lags_workspace_bytes(N, T, lag_min, lag_max, params)
+ * Every E in optE needs E+1 candidates in its window, else EDM_ERR_INVALID.
+ * Synchronises `stream` once (reads optE).
+ */
+int edm_ccm_rho_lags(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE, int32_t lag_min,
+                     int32_t lag_max, const edm_params *params, float *rho, int64_t ld_rho, void *ws,
+                     size_t ws_bytes, void *stream);
+size_t edm_ccm_rho_lags_workspace_bytes(int64_t N, int64_t T, int32_t lag_min, int32_t lag_max,
+                                        const edm_params *params);
 
 /*
  * Both phases end to end with HOST buffers (the problem as the paper states

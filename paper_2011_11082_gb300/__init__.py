@@ -20,6 +20,7 @@ from ._abi import (
     EDM_PRECISION_FP32,
     EDM_FLAG_LOOKUP_SCALAR,
     EDM_FLAG_VALIDATE,
+    EDM_FLAG_KNN_WARP,
     EdmError,
     edm_params,
 )
@@ -30,6 +31,7 @@ __all__ = [
     "edm_ccm_rho",
     "edm_ccm_workspace_bytes",
     "edm_ccm_host",
+    "edm_ccm_rho_lags",
     "edm_ccm_rho_backward",
     "edm_ccm_backward_workspace_bytes",
     "edm_ccm_rho_batched",
@@ -83,7 +85,8 @@ def edm_optimal_E(Y: torch.Tensor, E_max: int = 20, tau: int = 1, Tp: int = 1, r
     return optE, rho
 
 
-def edm_knn_table(Y: torch.Tensor, E: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0, stream=None):
+def edm_knn_table(Y: torch.Tensor, E: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0, stream=None,
+                  flags: int = 0):
     """Phase-2 kNN tables of every row of Y at dimension E:
     idx int32[n][Tq][E+1] (neighbour times, unshifted) and w float32[n][Tq][E+1]."""
     lib = _abi.load()
@@ -94,7 +97,7 @@ def edm_knn_table(Y: torch.Tensor, E: int, tau: int = 1, Tp: int = 1, exclusion_
         raise ValueError("series too short for this E")
     idx = torch.empty((n, Tq, E + 1), dtype=torch.int32, device=Y.device)
     w = torch.empty((n, Tq, E + 1), dtype=torch.float32, device=Y.device)
-    p = make_params(E_max=E, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius)
+    p = make_params(E_max=E, tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, flags=flags)
     st = lib.edm_knn_table(Y.data_ptr(), n, T, _ld(Y), E, ctypes.byref(p), idx.data_ptr(), w.data_ptr(), Tq,
                            _stream(stream))
     _abi.check(st, "edm_knn_table")
@@ -144,6 +147,31 @@ def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_cou
     st = lib.edm_ccm_rho(Y.data_ptr(), N, T, _ld(Y), optE.data_ptr(), lib_begin, lib_count, ctypes.byref(p),
                          out.data_ptr(), _ld(out), workspace.data_ptr(), workspace.numel(), _stream(stream))
     _abi.check(st, "edm_ccm_rho")
+    return out
+
+
+def edm_ccm_rho_lags(Y: torch.Tensor, optE: torch.Tensor, lag_min: int, lag_max: int, tau: int = 1,
+                     exclusion_radius: int = 0, precision: int = EDM_PRECISION_FP32, out: torch.Tensor | None = None,
+                     workspace: torch.Tensor | None = None, stream=None, flags: int = 0) -> torch.Tensor:
+    """Time-delay cross mapping: out[l - lag_min][j][i] = rho_l(library i ->
+    target j) for every lag in lag_min..lag_max, one table per (library, E)."""
+    lib = _abi.load()
+    Y = _dev_f32(Y, "Y")
+    N, T = Y.shape
+    if not (optE.is_cuda and optE.dtype == torch.int32 and optE.numel() == N and optE.is_contiguous()):
+        raise TypeError("optE must be a contiguous int32 CUDA tensor of N entries")
+    n_lags = lag_max - lag_min + 1
+    if out is None:
+        out = torch.empty((n_lags, N, N), dtype=torch.float32, device=Y.device)
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and tuple(out.shape[:2]) == (n_lags, N)):
+        raise TypeError("out must be a contiguous float32 CUDA tensor [n_lags][N][>=N]")
+    p = make_params(tau=tau, Tp=max(lag_max, 0), exclusion_radius=exclusion_radius, precision=precision, flags=flags)
+    need = int(lib.edm_ccm_rho_lags_workspace_bytes(N, T, lag_min, lag_max, ctypes.byref(p)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)
+    st = lib.edm_ccm_rho_lags(Y.data_ptr(), N, T, _ld(Y), optE.data_ptr(), lag_min, lag_max, ctypes.byref(p),
+                              out.data_ptr(), out.shape[2], workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _abi.check(st, "edm_ccm_rho_lags")
     return out
 
 

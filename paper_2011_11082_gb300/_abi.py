@@ -20,6 +20,7 @@ EDM_PRECISION_FP32 = 0
 EDM_PRECISION_FP16_TARGETS = 1
 EDM_FLAG_LOOKUP_SCALAR = 1
 EDM_FLAG_VALIDATE = 2
+EDM_FLAG_KNN_WARP = 4
 
 
 class edm_params(ctypes.Structure):
@@ -56,6 +57,9 @@ SIGNATURES = {
     "edm_knn_table": (ctypes.c_int, [_vp, _i64, _i64, _i64, _i32, _pp, _vp, _vp, _i64, _vp]),
     "edm_ccm_rho": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i64, _i64, _pp, _vp, _i64, _vp, ctypes.c_size_t, _vp]),
     "edm_ccm_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _pp]),
+    "edm_ccm_rho_lags": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i32, _i32, _pp, _vp, _i64, _vp, ctypes.c_size_t,
+                                        _vp]),
+    "edm_ccm_rho_lags_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i32, _i32, _pp]),
     "edm_ccm_host": (ctypes.c_int, [_vp, _i64, _i64, _pp, _vp, _vp, _i64, _i64, _vp, ctypes.c_size_t, _vp]),
     "edm_ccm_host_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i64, _pp]),
     "edm_ccm_rho_noalloc": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i64, _i64, _pp, _vp, _i64, _vp]),

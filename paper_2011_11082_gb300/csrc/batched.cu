@@ -285,6 +285,8 @@ cudaError_t enqueue_front(const edm_dataset &d, const SetPlan &sp, const SetPtrs
 
 cudaError_t enqueue_knn(const edm_dataset &d, const SetPtrs &P, const edm_params *p, int q_per_cta, cudaStream_t st)
 {
+    // the E in use are known on the device only: the warp kernel serves them
+    // all in one sweep
     return launch_knn_tables(d.Y, d.ldY, 0, (int)d.N, (int)d.T, p->tau, p->Tp, p->exclusion_radius,
                              (1u << p->E_max) - 1u, all_e_layout(d.T, p), P.tables, st, q_per_cta, P.sel);
 }
@@ -302,6 +304,8 @@ cudaError_t enqueue_lookup(const edm_dataset &d, const SetPlan &sp, const SetPtr
     a.T = (int)d.T;
     a.tau = p->tau;
     a.Tp = p->Tp;
+    a.s_lo = 0;
+    a.lag = p->Tp;
     a.tile_begin = 0;
     a.n_tiles = sp.n_tiles_max;
     a.n_lib = (int)d.N;

@@ -231,6 +231,8 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
             a.T = (int)T;
             a.tau = params->tau;
             a.Tp = params->Tp;
+            a.s_lo = 0;
+            a.lag = params->Tp;
             a.tile_begin = tile0;
             a.n_tiles = ntE;
             a.n_lib = nlb;

@@ -44,9 +44,9 @@ struct LaunchScope {
     ProfRec rec{};
     bool on;
     cudaStream_t st;
-    LaunchScope(int kernel, cudaStream_t s, double units) : on(g_prof), st(s)
+    LaunchScope(int kernel, cudaStream_t s, double units, int launches = 1) : on(g_prof), st(s)
     {
-        g_launches[kernel]++;
+        g_launches[kernel] += launches;
         if (on) {
             rec.kernel = kernel;
             rec.units = units;
@@ -353,7 +353,8 @@ int edm_knn_table(const float *Y, int64_t n_lib, int64_t T, int64_t ldY, int32_t
     {
         LaunchScope ls(EDM_KERNEL_KNN, (cudaStream_t)stream, (double)n_lib);
         EDM_CUDA(edm::launch_knn_public(Y, ldY, (int)n_lib, (int)T, E, params->tau, params->Tp,
-                                        params->exclusion_radius, idx, w, (cudaStream_t)stream));
+                                        params->exclusion_radius, idx, w, (cudaStream_t)stream,
+                                        (params->flags & EDM_FLAG_KNN_WARP) != 0));
     }
     return EDM_OK;
 }
@@ -457,10 +458,20 @@ int ccm_prepare(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
     return EDM_OK;
 }
 
+// Time-delay form: lags lag_min .. lag_min + n_lags - 1 cross-mapped from the
+// same tables (queries and candidates from s_lo on); omom holds the
+// observation sums of each lag ([n_lags][N]); lag l writes rho + l * stride.
+struct LagSpec {
+    int lag_min, n_lags, s_lo;
+    const float2 *omom;
+    int64_t rho_stride;
+};
+
 // Cross map of libraries [lib_begin, lib_begin + lib_count) into rho
 // (target-major, ld_rho) with a prepared plan.
 int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t ldY, int64_t lib_begin,
-                int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, cudaStream_t st)
+                int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, cudaStream_t st,
+                const LagSpec *lags = nullptr)
 {
     const CcmWs &L = P.L;
     const std::vector<edm::TileMeta> &tiles = P.tiles;
@@ -490,8 +501,10 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
             const int nlb = (int)std::min<int64_t>(per_block, lib_count - lb0);
             {
                 LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel));
-                EDM_CUDA(edm::launch_knn_tables(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
-                                                params->exclusion_radius, sel, lay, tables_d, st));
+                EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
+                                                     params->exclusion_radius, sel, lay, tables_d, st,
+                                                     (params->flags & EDM_FLAG_KNN_WARP) != 0,
+                                                     lags ? lags->s_lo : 0));
             }
             int64_t targets = 0;
             for (int t = tb0; t < tb0 + ntb; ++t)
@@ -506,6 +519,8 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
             a.T = (int)T;
             a.tau = params->tau;
             a.Tp = params->Tp;
+            a.s_lo = 0;
+            a.lag = params->Tp;
             a.n_lib = nlb;
             a.rho_col0 = lb0;
             a.rho = rho;
@@ -531,8 +546,17 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
                 a.n_tiles = ntb;
                 int parts = (4 * sms + ntb - 1) / ntb;
                 a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
-                LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                EDM_CUDA(edm::launch_lookup_multi(a, P.RB, st));
+                const int n_lk = lags ? lags->n_lags : 1;
+                for (int li = 0; li < n_lk; ++li) {
+                    if (lags) {
+                        a.s_lo = lags->s_lo;
+                        a.lag = lags->lag_min + li;
+                        a.omom = lags->omom + (size_t)li * N;
+                        a.rho = rho + li * lags->rho_stride;
+                    }
+                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
+                    EDM_CUDA(edm::launch_lookup_multi(a, P.RB, st));
+                }
             }
         }
     }
@@ -569,6 +593,68 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
     if (rc)
         return rc;
     return ccm_execute(P, Y, N, T, ldY, lib_begin, lib_count, params, rho, ld_rho, st);
+}
+
+size_t edm_ccm_rho_lags_workspace_bytes(int64_t N, int64_t T, int32_t lag_min, int32_t lag_max,
+                                        const edm_params *params)
+{
+    if (!params || N < 1 || T < 2 || lag_max < lag_min)
+        return 0;
+    edm_params pe = *params;
+    pe.Tp = std::max(lag_max, 0);
+    return ccm_ws_layout(N, T, &pe).total + align256((size_t)(lag_max - lag_min + 1) * N * sizeof(float2));
+}
+
+int edm_ccm_rho_lags(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE, int32_t lag_min,
+                     int32_t lag_max, const edm_params *params, float *rho, int64_t ld_rho, void *ws, size_t ws_bytes,
+                     void *stream)
+{
+    if (!params || lag_max < lag_min || lag_max - lag_min >= 4096 || lag_max > 65535 || lag_min < -65535)
+        return EDM_ERR_INVALID;
+    edm_params pe = *params;
+    pe.Tp = std::max(lag_max, 0);
+    int rc = ccm_validate(N, T, ldY, &pe);
+    if (rc)
+        return rc;
+    if (pe.flags & EDM_FLAG_LOOKUP_SCALAR)
+        return EDM_ERR_UNSUPPORTED;
+    if (!Y || !optE || !rho || !ws || ld_rho < N)
+        return EDM_ERR_INVALID;
+    const int n_lags = lag_max - lag_min + 1;
+    const int s_lo = std::max(0, -lag_min);
+    const size_t base = ccm_ws_layout(N, T, &pe).total;
+    if (ws_bytes < base + align256((size_t)n_lags * N * sizeof(float2)))
+        return EDM_ERR_WORKSPACE;
+    if ((rc = validate_series(Y, N, T, ldY, &pe, (cudaStream_t)stream)) != EDM_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> E_host((size_t)N);
+    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaStreamSynchronize(st));
+    for (int64_t j = 0; j < N; ++j) {  // every lag's window must hold k neighbours
+        const int E = E_host[(size_t)j];
+        if (E < 1 || E > EDM_MAX_E)
+            return EDM_ERR_INVALID;
+        const int64_t A = std::max<int64_t>((int64_t)(E - 1) * pe.tau, s_lo);
+        int64_t cand = (T - pe.Tp) - A;
+        if (pe.exclusion_radius >= 0)
+            cand -= 2 * (int64_t)pe.exclusion_radius + 1;
+        if (cand < E + 1)
+            return EDM_ERR_INVALID;
+    }
+    CcmPlan P;
+    rc = ccm_prepare(Y, N, T, ldY, E_host.data(), &pe, ws, st, P);
+    if (rc)
+        return rc;
+    float2 *omom_l = (float2 *)((unsigned char *)ws + base);
+    {
+        LaunchScope ls(EDM_KERNEL_PREP, st, (double)N * n_lags, n_lags);
+        for (int li = 0; li < n_lags; ++li)
+            EDM_CUDA(edm::launch_obs_moments(P.tiles_d, P.RB, P.meta_d, (int)P.tiles.size(), (int)T, pe.tau, pe.Tp,
+                                             s_lo, lag_min + li, omom_l + (size_t)li * N, st));
+    }
+    LagSpec spec{lag_min, n_lags, s_lo, omom_l, N * ld_rho};
+    return ccm_execute(P, Y, N, T, ldY, 0, N, &pe, rho, ld_rho, st, &spec);
 }
 
 size_t edm_ccm_host_workspace_bytes(int64_t N, int64_t T, int64_t block, const edm_params *params)
@@ -756,8 +842,9 @@ int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, cons
         const int nlb = (int)std::min<int64_t>(per_block, N - lb0);
         {
             LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel));
-            EDM_CUDA(edm::launch_knn_tables(Y, ldY, lb0, nlb, (int)T, params->tau, params->Tp,
-                                            params->exclusion_radius, sel, lay, wsb + L.tables, st));
+            EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lb0, nlb, (int)T, params->tau, params->Tp,
+                                                 params->exclusion_radius, sel, lay, wsb + L.tables, st,
+                                                 (params->flags & EDM_FLAG_KNN_WARP) != 0));
         }
         edm::BwArgs a;
         a.Y = Y;

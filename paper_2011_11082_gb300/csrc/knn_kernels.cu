@@ -240,7 +240,7 @@ struct EmitPublic {
 template <int J, bool kPublic>
 __global__ void __launch_bounds__(kKnnThreads, 2)
     knn_tables_kernel(const float *__restrict__ Y, int64_t ldY, int64_t lib0, int T, int tau, int Tp, int excl,
-                      uint32_t sel, int q_per_cta, int front, const __grid_constant__ TableLayout lay,
+                      uint32_t sel, int q_per_cta, int front, int s_lo, const __grid_constant__ TableLayout lay,
                       uint8_t *__restrict__ tables,
                       int32_t *__restrict__ pub_idx, float *__restrict__ pub_w, int pub_E,
                       const uint32_t *__restrict__ sel_dev)
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
         return;
     const int E_hi = 32 - __clz(sel);  // highest selected E
     int E_lo = __ffs(sel);             // lowest selected E
-    const int t_first = max(blockIdx.x * q_per_cta, (E_lo - 1) * tau);
+    // queries and candidates start at s_lo as well (0 for the plain cross map)
+    const int t_first = max(max((int)blockIdx.x * q_per_cta, (E_lo - 1) * tau), s_lo);
     const int t_stop = min((int)(blockIdx.x + 1) * q_per_cta, T - Tp);
 
     EmitInternal ei{tables + (size_t)lib * lay.lib_stride, &lay, 0, tau, Tp};
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
         q.xq = x;
         q.xc = x;
         q.t = t;
-        q.s_first = 0;
+        q.s_first = s_lo;
         q.s_last = T - 1 - Tp;
         q.tau = tau;
         q.same = 1;
@@ -344,7 +345,7 @@ cudaError_t launch_simplex(const float *Y, int64_t N, int T, int64_t ldY, int E_
 }
 
 template <int J, bool kPublic>
-static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
+static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl, int s_lo,
                          uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw, int pE,
                          cudaStream_t st, int q_per_cta, const uint32_t *sel_dev)
 {
@@ -357,37 +358,56 @@ static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, i
         return e;
     dim3 grid((unsigned)((T - Tp + q_per_cta - 1) / q_per_cta), (unsigned)n_lib);
     knn_tables_kernel<J, kPublic><<<grid, kKnnThreads, smem, st>>>(Y, ldY, lib0, T, tau, Tp, excl, sel, q_per_cta,
-                                                                    front, lay, tables, pidx, pw, pE, sel_dev);
+                                                                    front, s_lo, lay, tables, pidx, pw, pE, sel_dev);
     return cudaGetLastError();
 }
 
 template <bool kPublic>
-static cudaError_t knn_dispatch(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
+static cudaError_t knn_dispatch(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl, int s_lo,
                                 uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw,
                                 int pE, cudaStream_t st, int q = 64, const uint32_t *sel_dev = nullptr)
 {
-    switch (pick_J(T - Tp)) {
-    case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    case 24: return knn_J<24, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    switch (pick_J(T - Tp - s_lo)) {
+    case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 24: return knn_J<24, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
     }
 }
 
 cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
                               uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st, int q_per_cta,
-                              const uint32_t *sel_dev)
+                              const uint32_t *sel_dev, int s_lo)
 {
-    return knn_dispatch<false>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, nullptr, nullptr, 1, st,
+    return knn_dispatch<false>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, nullptr, nullptr, 1, st,
                                q_per_cta, sel_dev);
 }
 
-cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
-                              int32_t *idx, float *w, cudaStream_t st)
+// The thread-per-query kernel for a single E <= knn_thread_max_E() at tau = 1;
+// the warp kernel otherwise.
+static bool use_thread_kernel(int tau, uint32_t sel, bool force_warp)
 {
+    return !force_warp && tau == 1 && __builtin_popcount(sel) == 1 && 32 - __builtin_clz(sel) <= knn_thread_max_E();
+}
+
+cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp,
+                                   int excl, uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
+                                   bool force_warp, int s_lo)
+{
+    if (!use_thread_kernel(tau, sel, force_warp))
+        return launch_knn_tables(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, st, 64, nullptr, s_lo);
+    return launch_knn_thread(Y, ldY, lib0, n_lib, T, Tp, excl, 32 - __builtin_clz(sel), lay, tables, st, nullptr,
+                             s_lo);
+}
+
+cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
+                              int32_t *idx, float *w, cudaStream_t st, bool force_warp)
+{
+    if (!force_warp && tau == 1 && E <= knn_thread_max_E())
+        return launch_knn_thread_public(Y, ldY, n_lib, T, E, Tp, excl, idx, w, st);
     TableLayout lay{};
-    return knn_dispatch<true>(Y, ldY, 0, n_lib, T, tau, Tp, excl, 1u << (E - 1), lay, nullptr, idx, w, E, st);
+    return knn_dispatch<true>(Y, ldY, 0, n_lib, T, tau, Tp, excl, 0, 1u << (E - 1), lay, nullptr, idx, w, E, st);
 }
 
 cudaError_t knn_counters(unsigned long long out[2], bool reset)
@@ -397,6 +417,11 @@ cudaError_t knn_counters(unsigned long long out[2], bool reset)
         const unsigned long long z[2] = {0ull, 0ull};
         e = cudaMemcpyToSymbol(g_knn_counts, z, sizeof z);
     }
+    unsigned long long th[2] = {0ull, 0ull};
+    if (e == cudaSuccess)
+        e = knn_thread_counters(th, reset);
+    out[0] += th[0];
+    out[1] += th[1];
     return e;
 }
 

@@ -30,9 +30,28 @@ struct TableLayout {
 // for every E whose bit is set in sel, written in the internal layout.
 // q_per_cta: query points per CTA; sel_dev (optional): device word ANDed
 // into sel (E set planned on the device).
+// s_lo: queries and candidates start at time s_lo (0 for the plain cross
+// map; the time-delay form keeps every negative lag inside the series).
 cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
                               uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
-                              int q_per_cta = 64, const uint32_t *sel_dev = nullptr);
+                              int q_per_cta = 64, const uint32_t *sel_dev = nullptr, int s_lo = 0);
+
+// Thread-per-query tables for one E (tau = 1, E <= knn_thread_max_E() = 6),
+// same results as the warp kernel (knn_thread.cu).
+int knn_thread_max_E();
+// sel_dev (optional): device E mask; the launch does nothing if bit E-1 is clear.
+cudaError_t launch_knn_thread(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int Tp, int excl, int E,
+                              const TableLayout &lay, uint8_t *tables, cudaStream_t st,
+                              const uint32_t *sel_dev = nullptr, int s_lo = 0);
+cudaError_t launch_knn_thread_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int Tp, int excl,
+                                     int32_t *idx, float *w, cudaStream_t st);
+cudaError_t knn_thread_counters(unsigned long long out[2], bool reset);
+// Tables for the E set `sel` with the cheaper kernel: thread-per-query when
+// tau = 1 and sel holds one E <= knn_thread_max_E(), else the warp kernel
+// (one launch either way).
+cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp,
+                                   int excl, uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
+                                   bool force_warp = false, int s_lo = 0);
 
 // FP64 re-rank / exhaustive-scan query counts of the kNN kernels on the
 // current device (synchronises); reset clears them.
@@ -40,7 +59,7 @@ cudaError_t knn_counters(unsigned long long out[2], bool reset);
 
 // Public table format: idx int32 [n_lib][Tq][E+1] (unshifted), w float [n_lib][Tq][E+1].
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
-                              int32_t *idx, float *w, cudaStream_t st);
+                              int32_t *idx, float *w, cudaStream_t st, bool force_warp = false);
 
 // Target tiles: one E each, time-major rows of 128 bytes (z-normalised):
 // FP32 tiles hold 32 targets ([T][32] float); FP16 tiles (flag kTileF16)
@@ -74,7 +93,19 @@ struct LookupArgs {
     int64_t rho_col0;   // column of the block's first library in rho
     float *rho;
     int64_t ld_rho;
+    // time-delay form: the tables were built for horizon Tp over queries
+    // and candidates t >= s_lo; this launch cross-maps at lag `lag`
+    // (gathers y(s + lag), observes y(t + lag)).  Plain cross map: s_lo = 0,
+    // lag = Tp (chunked kernels only).
+    int s_lo;
+    int lag;
 };
+
+// Observation sums (S_o, n S_oo - S_o^2) of every staged target at lag
+// `lag` over the query times max((E-1)tau, s_lo) .. T-1-Tp of its tile's E,
+// from the staged (FP32 or FP16) values.
+cudaError_t launch_obs_moments(const float *tiles, int RB, const TileMeta *meta, int n_tiles, int T, int tau, int Tp,
+                               int s_lo, int lag, float2 *omom, cudaStream_t st);
 
 size_t lookup_smem_bytes(int T);
 // All tiles in [tile_begin, tile_begin + n_tiles) must have this E.

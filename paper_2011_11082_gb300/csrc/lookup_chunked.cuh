@@ -115,7 +115,9 @@ __device__ __forceinline__ float gather_slot_sum(const float *red, int t)
     return s;
 }
 
-template <int K, bool F16, int RB>
+// kLag: the time-delay form (tables over t >= s_lo, lag shift); the plain
+// instantiation folds those terms away (s_lo = 0, lag = Tp).
+template <int K, bool F16, int RB, bool kLag = false>
 __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 {
     // RB-byte rows hold RB/16 chunks; FP32 chunks are 4 targets, FP16 chunks
@@ -141,8 +143,14 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
     const TileMeta m = a.meta[tile];
     const int E = K - 1;
     const int L = (E - 1) * a.tau;
+    // table rows [r_lo, Tq): queries t = L + r >= s_lo; gathers at the stored
+    // neighbour time + Tp shifted by lag - Tp, observations at t + lag
     const int Tq = a.T - a.Tp - L;
-    const int nblk = (Tq + 31) / 32;
+    const int r_lo = kLag ? max(0, a.s_lo - L) : 0;
+    const int nrows = Tq - r_lo;
+    const int nblk = (nrows + 31) / 32;
+    const int dshift = kLag ? a.lag - a.Tp : 0;
+    const int lag = kLag ? a.lag : a.Tp;
 
     {
         const float4 *src = reinterpret_cast<const float4 *>(
@@ -187,23 +195,23 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
             float wq[kPref ? K : 1], wq2[kPref2 ? K : 1];
             uint32_t iq[kPref ? K : 1], iq2[kPref2 ? K : 1];
             if (kPref) {
-                const bool v = lane < Tq;
+                const bool v = r_lo + lane < Tq;
 #pragma unroll
                 for (int n = 0; n < (kPref ? K : 1); ++n) {
-                    wq[n] = v ? __ldg(Wt + n * tq_pad + lane) : 0.f;
-                    iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane) : 0u;
+                    wq[n] = v ? __ldg(Wt + n * tq_pad + r_lo + lane) : 0.f;
+                    iq[n] = v ? (uint32_t)((int)__ldg(It + n * tq_pad + r_lo + lane) + dshift) : 0u;
                 }
             }
             if (kPref2) {
-                const bool v = lane + 32 < Tq;
+                const bool v = r_lo + lane + 32 < Tq;
 #pragma unroll
                 for (int n = 0; n < (kPref2 ? K : 1); ++n) {
-                    wq2[n] = v ? __ldg(Wt + n * tq_pad + lane + 32) : 0.f;
-                    iq2[n] = v ? (uint32_t)__ldg(It + n * tq_pad + lane + 32) : 0u;
+                    wq2[n] = v ? __ldg(Wt + n * tq_pad + r_lo + lane + 32) : 0.f;
+                    iq2[n] = v ? (uint32_t)((int)__ldg(It + n * tq_pad + r_lo + lane + 32) + dshift) : 0u;
                 }
             }
             for (int b = 0; b < nblk; ++b) {
-                const int row = b * 32 + lane;
+                const int row = r_lo + b * 32 + lane;
                 const bool valid = row < Tq;
                 float wn[K];
                 uint32_t Bn[K];
@@ -221,7 +229,7 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
                             wq[n] = wq2[n];
                             iq[n] = iq2[n];
                             wq2[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
-                            iq2[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
+                            iq2[n] = v ? (uint32_t)((int)__ldg(It + n * tq_pad + nrow) + dshift) : 0u;
                         }
                     } else {
                         const int nrow = row + 32;
@@ -229,17 +237,18 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 #pragma unroll
                         for (int n = 0; n < (kPref ? K : 1); ++n) {
                             wq[n] = v ? __ldg(Wt + n * tq_pad + nrow) : 0.f;
-                            iq[n] = v ? (uint32_t)__ldg(It + n * tq_pad + nrow) : 0u;
+                            iq[n] = v ? (uint32_t)((int)__ldg(It + n * tq_pad + nrow) + dshift) : 0u;
                         }
                     }
                 } else {
 #pragma unroll
                     for (int n = 0; n < K; ++n) {
                         wn[n] = valid ? __ldg(Wt + n * tq_pad + row) : 0.f;
-                        Bn[n] = base + (valid ? (uint32_t)__ldg(It + n * tq_pad + row) : 0u) * (uint32_t)RB + lane16;
+                        Bn[n] = base + (valid ? (uint32_t)((int)__ldg(It + n * tq_pad + row) + dshift) : 0u) *
+                                           (uint32_t)RB + lane16;
                     }
                 }
-                const uint32_t orow = valid ? (uint32_t)(L + row + a.Tp) : 0u;
+                const uint32_t orow = valid ? (uint32_t)(L + row + lag) : 0u;
                 const uint32_t Bo = base + orow * (uint32_t)RB + lane16;
                 uint16_t wh[F16 ? K : 1];
                 // packed weight pairs for the FP32 gathers (register budget:
@@ -339,7 +348,7 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
             if (lane < SET && t < m.count) {
                 const int64_t j = a.pi[m.first + t];
                 const float2 om = a.omom[m.first + t];
-                const float n = (float)Tq;
+                const float n = (float)nrows;
                 const float num = n * tot[2][st] - tot[0][st] * om.x;
                 const float den_p = n * tot[1][st] - tot[0][st] * tot[0][st];
                 const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;

@@ -13,6 +13,7 @@ size_t chunked_smem_bytes(int T, int RB) { return 128 + (size_t)T * RB + (size_t
 // One launch for a block of tiles of mixed E (and FP16/FP32 tiles): each
 // CTA runs the variant of its own tile, so a CTA only ever executes one
 // specialisation's code.
+template <bool kLag>
 __global__ void __launch_bounds__(kCkThreads, 1) EDM_MULTI_NAME(LookupArgs a)
 {
     const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
@@ -20,9 +21,9 @@ __global__ void __launch_bounds__(kCkThreads, 1) EDM_MULTI_NAME(LookupArgs a)
 #define EDM_MK(KK)                                                                                                     \
     case KK:                                                                                                           \
         if (f16 && KK <= kF16MaxK)                                                                                     \
-            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true, EDM_RB>(a);                                                     \
+            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true, EDM_RB, kLag>(a);                                                     \
         else                                                                                                           \
-            lookup_chunk_body<KK, false, EDM_RB>(a);                                                                           \
+            lookup_chunk_body<KK, false, EDM_RB, kLag>(a);                                                                           \
         break;
     switch (m.E + 1) {
         EDM_MK(2)
@@ -55,11 +56,15 @@ cudaError_t EDM_MULTI_LAUNCH(const LookupArgs &a, cudaStream_t st)
     if (a.n_tiles <= 0 || a.n_lib <= 0)
         return cudaSuccess;
     size_t smem = chunked_smem_bytes(a.T, EDM_RB);
-    cudaError_t e = cudaFuncSetAttribute(EDM_MULTI_NAME, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the time-delay form is a separate instantiation, so the plain cross
+    // map keeps its register allocation
+    const bool lag = a.s_lo != 0 || a.lag != a.Tp;
+    void (*kern)(LookupArgs) = lag ? EDM_MULTI_NAME<true> : EDM_MULTI_NAME<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
-    EDM_MULTI_NAME<<<grid, kCkThreads, smem, st>>>(a);
+    kern<<<grid, kCkThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

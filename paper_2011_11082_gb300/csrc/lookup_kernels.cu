@@ -11,6 +11,8 @@
 // (lane, r) are folded into per-target sums through a small shared
 // transpose at the end of the library.
 #include "edm_internal.cuh"
+#include <cuda_fp16.h>
+
 #include "launchers.h"
 
 namespace edm {
@@ -93,6 +95,53 @@ __global__ void __launch_bounds__(256) prep_targets_kernel(const float *__restri
             tile[(size_t)t * width + slot] = z;
         }
     }
+}
+
+// Observation sums at one lag over a table's query window (time-delay form).
+__global__ void __launch_bounds__(256) obs_moments_kernel(const float *__restrict__ tiles, int RB,
+                                                          const TileMeta *__restrict__ meta, int T, int tau, int Tp,
+                                                          int s_lo, int lag, float2 *__restrict__ omom)
+{
+    const TileMeta m = meta[blockIdx.x];
+    if (m.E == 0)
+        return;
+    const bool f16 = (m.flags & kTileF16) != 0;
+    const int words = RB / 4;  // 32-bit words per tile row
+    const int L = (m.E - 1) * tau;
+    const int t_lo = max(L, s_lo), t_hi = T - 1 - Tp;
+    const int lane = lane_id(), warp = warp_id();
+    const float *tile = tiles + (size_t)blockIdx.x * T * words;
+    for (int slot = warp; slot < m.count; slot += blockDim.x / 32) {
+        double so = 0.0, soo = 0.0;
+        for (int t = t_lo + lane; t <= t_hi; t += 32) {
+            const float *row = tile + (size_t)(t + lag) * words;
+            float z;
+            if (f16) {
+                const uint32_t u = __float_as_uint(row[slot % words]);
+                const unsigned short h = (unsigned short)(slot < words ? (u & 0xffffu) : (u >> 16));
+                z = __half2float(__ushort_as_half(h));
+            } else {
+                z = row[slot];
+            }
+            so += (double)z;
+            soo += (double)z * (double)z;
+        }
+        so = warp_sum_d(so);
+        soo = warp_sum_d(soo);
+        if (lane == 0) {
+            const double n = (double)(t_hi - t_lo + 1);
+            omom[m.first + slot] = make_float2((float)so, (float)(n * soo - so * so));
+        }
+    }
+}
+
+cudaError_t launch_obs_moments(const float *tiles, int RB, const TileMeta *meta, int n_tiles, int T, int tau, int Tp,
+                               int s_lo, int lag, float2 *omom, cudaStream_t st)
+{
+    if (n_tiles <= 0)
+        return cudaSuccess;
+    obs_moments_kernel<<<n_tiles, 256, 0, st>>>(tiles, RB, meta, T, tau, Tp, s_lo, lag, omom);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

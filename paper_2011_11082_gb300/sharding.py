@@ -47,3 +47,53 @@ def run_sharded(Y, compute_optE: Callable, compute_rows: Callable, world: int, r
     optE = all_gather_optE(torch.as_tensor(local, dtype=torch.int32), N, world, rank, group)
     rows = compute_rows(Y, optE, b, e)
     return optE, (b, e), rows
+
+
+def _wait_count(store, key: str, target: int, timeout_s: float):
+    """Block until the store counter `key` reaches `target` (bounded)."""
+    import time
+
+    t0 = time.monotonic()
+    while int(store.add(key, 0)) < target:
+        if time.monotonic() - t0 > timeout_s:
+            raise TimeoutError(f"{key}: {int(store.add(key, 0))} of {target} after {timeout_s:.0f} s")
+        time.sleep(0.002)
+
+
+def run_self_scheduled(Y, compute_optE: Callable, compute_rows: Callable, store, block: int = 64,
+                       phase1_block: int = 256, timeout_s: float = 600.0, tag: str = "edm"):
+    """Self-scheduling form of the paper's master-worker runtime (Sec. III-C):
+    every rank repeatedly takes the next unclaimed block from a shared atomic
+    counter in `store` (a torch.distributed Store: TCPStore, FileStore, ...)
+    until none are left, so fast ranks take more blocks.  Phase 1 runs over
+    blocks of series; each finished block publishes its optE in the store;
+    once all blocks are in, every rank reads the full optE (the paper's
+    broadcast) and phase 2 runs over blocks of library rows.  Returns
+    (optE [N] int32, [(row_begin, row_end, rows), ...] for the blocks this
+    rank computed).  `tag` separates independent runs on one store; the
+    store's server must outlive every rank's last call (synchronise the
+    ranks before the process hosting it exits)."""
+    import numpy as np
+
+    N = Y.shape[0]
+    n1 = (N + phase1_block - 1) // phase1_block
+    while True:
+        b = int(store.add(f"{tag}/p1/next", 1)) - 1
+        if b >= n1:
+            break
+        lo, hi = b * phase1_block, min(N, (b + 1) * phase1_block)
+        e = np.ascontiguousarray(np.asarray(compute_optE(Y[lo:hi]), dtype=np.int32))
+        store.set(f"{tag}/p1/optE/{b}", e.tobytes())
+        store.add(f"{tag}/p1/done", 1)
+    _wait_count(store, f"{tag}/p1/done", n1, timeout_s)
+    optE = np.concatenate([np.frombuffer(store.get(f"{tag}/p1/optE/{b}"), dtype=np.int32) for b in range(n1)])
+    optE_t = torch.from_numpy(optE.copy())
+    n2 = (N + block - 1) // block
+    mine = []
+    while True:
+        b = int(store.add(f"{tag}/p2/next", 1)) - 1
+        if b >= n2:
+            break
+        lo, hi = b * block, min(N, (b + 1) * block)
+        mine.append((lo, hi, compute_rows(Y, optE_t, lo, hi)))
+    return optE_t, mine

@@ -68,3 +68,60 @@ def test_two_ranks_match_single_process(tmp_path):
     ranges = [tuple(np.load(tmp_path / f"range_{r}.npy")) for r in range(2)]
     assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and ranges[1][1] == 13
     assert np.array_equal(np.concatenate(parts), R)
+
+
+def _ss_worker(rank, world, port, Y, E_max, out_dir):
+    from oracle import oracle as orc
+    from paper_2011_11082_gb300.sharding import run_self_scheduled
+
+    store = dist.TCPStore("127.0.0.1", port, world, is_master=(rank == 0), timeout=__import__("datetime").timedelta(seconds=120))
+
+    def opt(Ys):
+        return orc.optimal_E(Ys, E_max, nthreads=1)[0]
+
+    def rows(Yf, optE, b, e):
+        if rank == 0:  # a slow rank: the other one should take more blocks
+            __import__("time").sleep(0.05)
+        return orc.ccm_rho_rows(Yf, optE.numpy(), rows=np.arange(b, e), nthreads=1)
+
+    optE, blocks = run_self_scheduled(Y, opt, rows, store, block=2, phase1_block=3, timeout_s=120)
+    np.save(os.path.join(out_dir, f"ss_optE_{rank}.npy"), optE.numpy())
+    for lo, hi, R in blocks:
+        np.save(os.path.join(out_dir, f"ss_rows_{lo}_{hi}_{rank}.npy"), R)
+    # keep the master's store alive until every other rank has stopped using it
+    store.add("ss/finished", 1)
+    while int(store.add("ss/finished", 0)) < world:
+        __import__("time").sleep(0.01)
+    if rank != 0:
+        store.add("ss/left", 1)
+    else:
+        while int(store.add("ss/left", 0)) < world - 1:
+            __import__("time").sleep(0.01)
+
+
+def test_self_scheduled_ranks_cover_every_block_once(tmp_path):
+    """Three ranks pull phase-1 and phase-2 blocks from a shared counter:
+    every block is computed exactly once, the union equals the single-process
+    result, and a slower rank ends up with fewer blocks."""
+    from oracle import oracle as orc
+
+    Y = synth.coupled_logistic(14, 150, 0.1, 0.05, seed_data=23, seed_noise=24)
+    E_max = 4
+    port = _free_port()
+    mp.start_processes(_ss_worker, args=(3, port, Y, E_max, str(tmp_path)), nprocs=3, join=True, start_method="spawn")
+    oE, _ = orc.optimal_E(Y, E_max)
+    R = orc.ccm_rho_rows(Y, oE)
+    for r in range(3):
+        assert np.array_equal(np.load(tmp_path / f"ss_optE_{r}.npy"), oE)
+    got = np.full_like(R, np.nan)
+    owners = {}
+    for f in os.listdir(tmp_path):
+        if f.startswith("ss_rows_"):
+            lo, hi, r = (int(v) for v in f[len("ss_rows_"):-4].split("_"))
+            assert (lo, hi) not in owners
+            owners[(lo, hi)] = r
+            got[lo:hi] = np.load(tmp_path / f)
+    assert sorted(owners) == [(b, min(14, b + 2)) for b in range(0, 14, 2)]
+    assert np.array_equal(got, R)
+    counts = [sum(1 for v in owners.values() if v == r) for r in range(3)]
+    assert counts[0] <= max(counts[1], counts[2]), counts
