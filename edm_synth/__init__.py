@@ -17,6 +17,7 @@ from .coupled_maps import (
     sine_series,
     logistic_series,
     white_noise,
+    library_subsets,
 )
 
 __all__ = [
@@ -31,4 +32,5 @@ __all__ = [
     "sine_series",
     "logistic_series",
     "white_noise",
+    "library_subsets",
 ]

@@ -186,3 +186,20 @@ def logistic_series(T: int, r: float = 3.8, x0: float = 0.4, burn_in: int = 100)
 
 def white_noise(T: int, seed: int = 7) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(T).astype(np.float32)
+
+
+def library_subsets(T: int, lo: int, hi: int, sizes, samples: int, seed: int = 8) -> np.ndarray:
+    """Random library subsets for the convergence test: for each size L in
+    `sizes` and each of `samples` draws, L distinct times from [lo, hi]
+    without replacement, as bit masks uint32[len(sizes) * samples][ceil(T/32)]
+    (bit s of word s // 32 = time s allowed), size-major."""
+    rng = np.random.default_rng(seed)
+    words = (T + 31) // 32
+    out = np.zeros((len(sizes) * samples, words), np.uint32)
+    pool = np.arange(lo, hi + 1)
+    for a, L in enumerate(sizes):
+        for b in range(samples):
+            pick = rng.choice(pool, size=int(L), replace=False)
+            row = out[a * samples + b]
+            np.bitwise_or.at(row, pick // 32, (np.uint32(1) << (pick % 32).astype(np.uint32)))
+    return out

@@ -101,6 +101,37 @@ static int knn_query(const double *xq, int64_t t, const double *xc, int64_t s_lo
     return n;
 }
 
+/* knn_query restricted to the candidates whose bit is set in `mask`
+ * (bit s of word s / 32): a library subset for the convergence test. */
+static int knn_query_masked(const double *x, int64_t t, int64_t s_lo, int64_t s_hi, const uint32_t *mask, int E,
+                            int tau, int excl, int k, int64_t *idx, double *d2)
+{
+    int n = 0;
+    for (int64_t s = s_lo; s <= s_hi; ++s) {
+        if (!((mask[s / 32] >> (s % 32)) & 1u))
+            continue;
+        if (excl >= 0 && llabs(s - t) <= excl)
+            continue;
+        double d = embed_dist2(x, t, x, s, E, tau);
+        int pos;
+        if (n < k) {
+            pos = n++;
+        } else if (pair_before(d, s, d2[k - 1], idx[k - 1])) {
+            pos = k - 1;
+        } else {
+            continue;
+        }
+        while (pos > 0 && pair_before(d, s, d2[pos - 1], idx[pos - 1])) {
+            d2[pos] = d2[pos - 1];
+            idx[pos] = idx[pos - 1];
+            --pos;
+        }
+        d2[pos] = d;
+        idx[pos] = s;
+    }
+    return n;
+}
+
 /* Distances (squared) of one kNN row -> normalised exponential weights. */
 static void simplex_weights(const double *d2, int k, double *w)
 {
@@ -505,6 +536,75 @@ int orc_ccm_rho_lags(const double *Y, int64_t N, int64_t T, int64_t ldY, const i
     }
     (void)nthreads;
     (void)n_lags;
+    return rc_all;
+}
+
+/*
+ * CCM convergence (the library-size test of the original CCM that the paper
+ * leaves out, Sec. III-A): the cross map of every library row with its
+ * candidate points restricted to a subset -- bit s of mask[u * words + s/32]
+ * set -- for each of n_sub subsets; queries are all points
+ * t in [(E-1)tau, T-1-Tp] as in the plain cross map.  With every bit set it
+ * is exactly that cross map.  rho is [n_sub][n_rows][N].
+ */
+int orc_ccm_rho_subsets(const double *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                        const int64_t *rows, int64_t n_rows, const uint32_t *masks, int64_t n_sub, int64_t words,
+                        int tau, int Tp, int excl, double *rho, int nthreads)
+{
+    if (N < 1 || T < 2 || ldY < T || tau < 1 || Tp < 0 || n_rows < 0 || n_sub < 1 || words * 32 < T)
+        return ORC_ERR_INVALID;
+    int E_top = 0;
+    for (int64_t j = 0; j < N; ++j) {
+        if (optE[j] < 1)
+            return ORC_ERR_INVALID;
+        if (optE[j] > E_top)
+            E_top = optE[j];
+    }
+    int rc_all = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads < 1)
+        nthreads = 1;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t u = 0; u < n_sub; ++u)
+        for (int64_t r = 0; r < n_rows; ++r) {
+            const double *x = Y + rows[r] * ldY;
+            const uint32_t *mask = masks + u * words;
+            for (int E = 1; E <= E_top; ++E) {
+                int used = 0;
+                for (int64_t j = 0; j < N && !used; ++j)
+                    used = optE[j] == E;
+                if (!used)
+                    continue;
+                int64_t L = (int64_t)(E - 1) * tau;
+                int64_t nq = orc_ccm_rows(T, E, tau, Tp);
+                int k = E + 1;
+                int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nq * k));
+                double *w = (double *)malloc(sizeof(double) * (size_t)(nq * k));
+                double *d2 = (double *)malloc(sizeof(double) * (size_t)k);
+                int rc = (idx && w && d2 && nq > 0) ? ORC_OK : ORC_ERR_NOMEM;
+                for (int64_t q = 0; rc == ORC_OK && q < nq; ++q) {
+                    if (knn_query_masked(x, L + q, L, T - 1 - Tp, mask, E, tau, excl, k, idx + q * k, d2) < k)
+                        rc = ORC_ERR_INVALID;
+                    else
+                        simplex_weights(d2, k, w + q * k);
+                }
+                if (rc == ORC_OK) {
+                    for (int64_t j = 0; j < N; ++j)
+                        if (optE[j] == E)
+                            rho[(u * n_rows + r) * N + j] = orc_lookup_rho(Y + j * ldY, T, E, tau, Tp, idx, w);
+                } else {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                    rc_all = rc;
+                }
+                free(idx);
+                free(w);
+                free(d2);
+            }
+        }
+    (void)nthreads;
     return rc_all;
 }
 

@@ -78,6 +78,9 @@ def _declare(lib):
     lib.orc_ccm_rho_lags.restype = _int
     lib.orc_ccm_rho_lags.argtypes = [_dp, _i64, _i64, _i64, _i32p, _i64p, _i64, _int, _int, _int, _int, _dp,
                                      _int]
+    lib.orc_ccm_rho_subsets.restype = _int
+    lib.orc_ccm_rho_subsets.argtypes = [_dp, _i64, _i64, _i64, _i32p, _i64p, _i64, ctypes.POINTER(ctypes.c_uint32), _i64,
+                                        _i64, _int, _int, _int, _dp, _int]
     lib.orc_max_threads.restype = _int
     lib.orc_max_threads.argtypes = []
     return lib
@@ -241,6 +244,25 @@ def ccm_rho_lags(Y, optE, lag_min, lag_max, rows=None, tau=1, excl=0, nthreads=N
                                            tau, lag_min, lag_max, excl, _ptr(rho, _dp), nthreads or default_threads())
     if rc:
         raise ValueError(f"orc_ccm_rho_lags failed ({rc})")
+    return rho
+
+
+def ccm_rho_subsets(Y, optE, masks, rows=None, tau=1, Tp=1, excl=0, nthreads=None, lib=None):
+    """CCM convergence: rho[u][r][j] = rho(library rows[r] -> target j) with
+    the library's candidate points restricted to subset u (masks: uint32
+    [n_sub][words], bit s = candidate time s allowed)."""
+    Y = _f64(np.atleast_2d(Y))
+    N, T = Y.shape
+    optE = np.ascontiguousarray(optE, dtype=np.int32)
+    masks = np.ascontiguousarray(np.atleast_2d(masks), dtype=np.uint32)
+    rows = np.arange(N, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    rho = np.full((masks.shape[0], rows.size, N), np.nan, np.float64)
+    rc = (lib or _load()).orc_ccm_rho_subsets(_ptr(Y, _dp), N, T, T, _ptr(optE, _i32p), _ptr(rows, _i64p), rows.size,
+                                              _ptr(masks, ctypes.POINTER(ctypes.c_uint32)), masks.shape[0],
+                                              masks.shape[1], tau, Tp, excl, _ptr(rho, _dp),
+                                              nthreads or default_threads())
+    if rc:
+        raise ValueError(f"orc_ccm_rho_subsets failed ({rc})")
     return rho
 
 

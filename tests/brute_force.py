@@ -142,3 +142,22 @@ def ccm_lags_pair(x_lib, y_tgt, E, lags, tau=1, excl=0) -> np.ndarray:
         pred = (w * y[idx + lag]).sum(axis=1)
         out.append(corr(y[times + lag], pred))
     return np.array(out)
+
+
+def ccm_pair_subset(x_lib, y_tgt, E, allowed, tau=1, Tp=1, excl=0) -> float:
+    """Plain cross map with the candidate points restricted to the set
+    `allowed` of times (queries: every embedded point)."""
+    x = np.asarray(x_lib, np.float64)
+    y = np.asarray(y_tgt, np.float64)
+    T = x.size
+    L = (E - 1) * tau
+    times = np.arange(L, T - Tp)
+    V = embed(x, E, tau)[: T - Tp - L]
+    keep = np.array([t in allowed for t in times])
+    D = distance_matrix(V, V[keep])
+    ct = times[keep]
+    mask = np.abs(times[:, None] - ct[None, :]) > excl if excl >= 0 else None
+    idx, d2 = neighbours(D, ct, E + 1, mask)
+    w = np.stack([exp_weights(r) for r in d2])
+    pred = (w * y[idx + Tp]).sum(axis=1)
+    return corr(y[times + Tp], pred)

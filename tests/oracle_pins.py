@@ -252,6 +252,35 @@ def pin_lags_integer_period_sine(lib=None):
     assert np.all(np.abs(R - 1.0) < 1e-12), R
 
 
+def _mask_times(mask_row, T):
+    return {s for s in range(T) if (int(mask_row[s // 32]) >> (s % 32)) & 1}
+
+
+def pin_subsets_brute(lib=None):
+    """Convergence cross map (library subsets) against the per-pair brute
+    force, with and without exclusion."""
+    Y = _tiny_series(17, N=3, T=48)
+    optE = np.array([2, 1, 3], np.int32)
+    masks = synth.library_subsets(48, 2, 46, sizes=(14, 30), samples=2, seed=5)
+    for excl in (0, 2):
+        R = orc.ccm_rho_subsets(Y, optE, masks, excl=excl, nthreads=2, lib=lib)
+        for u in range(masks.shape[0]):
+            allowed = _mask_times(masks[u], 48)
+            for i in range(3):
+                for j in range(3):
+                    b = bf.ccm_pair_subset(Y[i], Y[j], int(optE[j]), allowed, excl=excl)
+                    assert abs(R[u, i, j] - b) < 1e-12, (excl, u, i, j)
+
+
+def pin_subsets_full_library_is_ccm(lib=None):
+    """Every candidate allowed: exactly the plain cross map."""
+    Y = _tiny_series(18, N=4, T=70)
+    optE = np.array([2, 3, 1, 2], np.int32)
+    full = np.full((1, 3), 0xFFFFFFFF, np.uint32)
+    R = orc.ccm_rho_subsets(Y, optE, full, nthreads=2, lib=lib)
+    assert np.array_equal(R[0], orc.ccm_rho_rows(Y, optE, nthreads=2, lib=lib))
+
+
 ALL_PINS = [
     pin_hand_example,
     pin_knn_brute,
@@ -272,4 +301,6 @@ ALL_PINS = [
     pin_lags_brute,
     pin_lags_reduce_to_ccm,
     pin_lags_integer_period_sine,
+    pin_subsets_brute,
+    pin_subsets_full_library_is_ccm,
 ]

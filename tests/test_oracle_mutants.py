@@ -24,7 +24,9 @@ MUTANTS = {
     "weights_not_normalised": ("w[n] = w[n] / sum;", "w[n] = w[n] / (sum + 1.0);"),
     "distance_not_squared": ("double sq = diff * diff;", "double sq = fabs(diff);"),
     "tie_break_reversed": ("(da == db && ia < ib)", "(da == db && ia > ib)"),
-    "exclusion_off_by_one": ("llabs(s - t) <= excl", "llabs(s - t) < excl"),
+    "exclusion_off_by_one": ("same && excl >= 0 && llabs(s - t) <= excl", "same && excl >= 0 && llabs(s - t) < excl"),
+    "subset_exclusion_off_by_one": ("        if (excl >= 0 && llabs(s - t) <= excl)\n            continue;\n        double d = embed_dist2(x, t, x, s",
+                                    "        if (excl >= 0 && llabs(s - t) < excl)\n            continue;\n        double d = embed_dist2(x, t, x, s"),
     "phase1_split_rounded_up": ("int64_t h = T / 2;", "int64_t h = (T + 1) / 2;"),
     "phase1_future_from_target": ("p = p + w[n] * lib[idx[n] + Tp];", "p = p + w[n] * tgt[idx[n] + Tp];"),
     "pearson_uncentred_b": ("double da = a[i] - ma, db = b[i] - mb;", "double da = a[i] - ma, db = b[i];"),
@@ -36,6 +38,7 @@ MUTANTS = {
     "lags_observation_unshifted": ("obs[q] = y[A + q + l];", "obs[q] = y[A + q];"),
     "lags_window_start_shifted": ("int64_t A = L > -(int64_t)lag_min ? L : -(int64_t)lag_min;",
                                   "int64_t A = 1 + (L > -(int64_t)lag_min ? L : -(int64_t)lag_min);"),
+    "subset_mask_inverted": ("if (!((mask[s / 32] >> (s % 32)) & 1u))", "if (((mask[s / 32] >> (s % 32)) & 1u))"),
     "table_query_window_shifted": ("int got = knn_query(x, t, x, t_lo, t_hi, E, tau, 1, excl, k, idx + r * k, d2);",
                                    "int got = knn_query(x, t, x, t_lo, t_hi - 1, E, tau, 1, excl, k, idx + r * k, d2);"),
 }
