@@ -152,6 +152,25 @@ size_t edm_ccm_rho_lags_workspace_bytes(int64_t N, int64_t T, int32_t lag_min, i
                                         const edm_params *params);
 
 /*
+ * CCM convergence (the library-size test of the original CCM that the paper
+ * leaves out, Sec. III-A): the cross map of every library (as edm_ccm_rho
+ * with all N libraries) with each library's candidate points restricted to
+ * a subset, for n_sub subsets; queries are every embedded point.  The
+ * subsets are inputs (draw them with any seeded generator): subset u allows
+ * candidate time s when bit s of masks[u * words + s / 32] is set.
+ * Averaging rho over subsets of equal size L gives the convergence curve
+ * rho(L).  With every bit set the result is edm_ccm_rho's.
+ *   masks  DEVICE uint32 [n_sub][words], words >= ceil(T / 32)
+ *   rho    [n_sub][N][ld_rho] target-major per subset
+ *   ws     edm_ccm_workspace_bytes(N, T, params)
+ * Each subset must leave E+1 candidates (beyond the exclusion window) for
+ * the largest E in optE, else EDM_ERR_INVALID.  Synchronises `stream` once.
+ */
+int edm_ccm_rho_subsets(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                        const uint32_t *masks, int32_t n_sub, int64_t words, const edm_params *params, float *rho,
+                        int64_t ld_rho, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Both phases end to end with HOST buffers (the problem as the paper states
  * it: series in, optimal E and the causal map out).  Copies Y to the device,
  * runs phase 1, reads optE back, then phase 2 in blocks of `block` libraries

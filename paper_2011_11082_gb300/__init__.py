@@ -32,6 +32,7 @@ __all__ = [
     "edm_ccm_workspace_bytes",
     "edm_ccm_host",
     "edm_ccm_rho_lags",
+    "edm_ccm_rho_subsets",
     "edm_ccm_rho_backward",
     "edm_ccm_backward_workspace_bytes",
     "edm_ccm_rho_batched",
@@ -172,6 +173,34 @@ def edm_ccm_rho_lags(Y: torch.Tensor, optE: torch.Tensor, lag_min: int, lag_max:
     st = lib.edm_ccm_rho_lags(Y.data_ptr(), N, T, _ld(Y), optE.data_ptr(), lag_min, lag_max, ctypes.byref(p),
                               out.data_ptr(), out.shape[2], workspace.data_ptr(), workspace.numel(), _stream(stream))
     _abi.check(st, "edm_ccm_rho_lags")
+    return out
+
+
+def edm_ccm_rho_subsets(Y: torch.Tensor, optE: torch.Tensor, masks: torch.Tensor, tau: int = 1, Tp: int = 1,
+                        exclusion_radius: int = 0, precision: int = EDM_PRECISION_FP32,
+                        out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """CCM convergence: out[u][j][i] = rho(library i -> target j) with each
+    library's candidates restricted to subset u (masks: int32/uint32 CUDA
+    tensor [n_sub][words], bit s = candidate time s allowed)."""
+    lib = _abi.load()
+    Y = _dev_f32(Y, "Y")
+    N, T = Y.shape
+    if not (optE.is_cuda and optE.dtype == torch.int32 and optE.numel() == N and optE.is_contiguous()):
+        raise TypeError("optE must be a contiguous int32 CUDA tensor of N entries")
+    if not (masks.is_cuda and masks.dtype in (torch.int32, torch.uint32) and masks.dim() == 2 and masks.is_contiguous()):
+        raise TypeError("masks must be a contiguous 32-bit CUDA tensor [n_sub][words]")
+    n_sub, words = masks.shape
+    if out is None:
+        out = torch.empty((n_sub, N, N), dtype=torch.float32, device=Y.device)
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    need = int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)
+    st = lib.edm_ccm_rho_subsets(Y.data_ptr(), N, T, _ld(Y), optE.data_ptr(), masks.data_ptr(), n_sub, words,
+                                 ctypes.byref(p), out.data_ptr(), out.shape[2], workspace.data_ptr(),
+                                 workspace.numel(), _stream(stream))
+    _abi.check(st, "edm_ccm_rho_subsets")
     return out
 
 

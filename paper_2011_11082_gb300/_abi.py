@@ -60,6 +60,8 @@ SIGNATURES = {
     "edm_ccm_rho_lags": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i32, _i32, _pp, _vp, _i64, _vp, ctypes.c_size_t,
                                         _vp]),
     "edm_ccm_rho_lags_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i32, _i32, _pp]),
+    "edm_ccm_rho_subsets": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _i32, _i64, _pp, _vp, _i64, _vp,
+                                           ctypes.c_size_t, _vp]),
     "edm_ccm_host": (ctypes.c_int, [_vp, _i64, _i64, _pp, _vp, _vp, _i64, _i64, _vp, ctypes.c_size_t, _vp]),
     "edm_ccm_host_workspace_bytes": (ctypes.c_size_t, [_i64, _i64, _i64, _pp]),
     "edm_ccm_rho_noalloc": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _i64, _i64, _pp, _vp, _i64, _vp]),

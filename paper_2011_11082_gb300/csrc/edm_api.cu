@@ -44,6 +44,7 @@ struct LaunchScope {
     ProfRec rec{};
     bool on;
     cudaStream_t st;
+    void add_launches(int kernel, int n) { g_launches[kernel] += n; }
     LaunchScope(int kernel, cudaStream_t s, double units, int launches = 1) : on(g_prof), st(s)
     {
         g_launches[kernel] += launches;
@@ -467,11 +468,21 @@ struct LagSpec {
     int64_t rho_stride;
 };
 
+// Convergence form: each library block's tables are built once per
+// candidate subset u (mask u of words 32-bit words) and cross-mapped into
+// rho + u * rho_stride.
+struct SubsetSpec {
+    const uint32_t *masks;
+    int n_sub;
+    int64_t words;
+    int64_t rho_stride;
+};
+
 // Cross map of libraries [lib_begin, lib_begin + lib_count) into rho
 // (target-major, ld_rho) with a prepared plan.
 int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t ldY, int64_t lib_begin,
                 int64_t lib_count, const edm_params *params, float *rho, int64_t ld_rho, cudaStream_t st,
-                const LagSpec *lags = nullptr)
+                const LagSpec *lags = nullptr, const SubsetSpec *subsets = nullptr)
 {
     const CcmWs &L = P.L;
     const std::vector<edm::TileMeta> &tiles = P.tiles;
@@ -497,14 +508,22 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
         const int64_t per_block = std::min<int64_t>(
             65535, std::max<int64_t>(std::min<int64_t>(kMinLibBlock, (int64_t)(L.table_cap / (size_t)lay.lib_stride)),
                                      (int64_t)(L.table_bytes / (size_t)lay.lib_stride)));
-        for (int64_t lb0 = 0; lb0 < lib_count; lb0 += per_block) {
+        for (int64_t lb0 = 0; lb0 < lib_count; lb0 += per_block)
+          for (int su = 0; su < (subsets ? subsets->n_sub : 1); ++su) {
             const int nlb = (int)std::min<int64_t>(per_block, lib_count - lb0);
             {
-                LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel));
-                EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
-                                                     params->exclusion_radius, sel, lay, tables_d, st,
-                                                     (params->flags & EDM_FLAG_KNN_WARP) != 0,
-                                                     lags ? lags->s_lo : 0));
+                int n_knn = 1;
+                LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel), 0);
+                if (subsets)  // candidate subsets: the warp kernel (mask test per candidate)
+                    EDM_CUDA(edm::launch_knn_tables(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
+                                                    params->exclusion_radius, sel, lay, tables_d, st, 64, nullptr, 0,
+                                                    subsets->masks + (size_t)su * subsets->words));
+                else
+                    EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau,
+                                                         params->Tp, params->exclusion_radius, sel, lay, tables_d, st,
+                                                         (params->flags & EDM_FLAG_KNN_WARP) != 0,
+                                                         lags ? lags->s_lo : 0, &n_knn));
+                ls.add_launches(EDM_KERNEL_KNN, n_knn);
             }
             int64_t targets = 0;
             for (int t = tb0; t < tb0 + ntb; ++t)
@@ -523,7 +542,7 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
             a.lag = params->Tp;
             a.n_lib = nlb;
             a.rho_col0 = lb0;
-            a.rho = rho;
+            a.rho = subsets ? rho + su * subsets->rho_stride : rho;
             a.ld_rho = ld_rho;
             if (scalar) {
                 // comparison path: one launch per run of equal E
@@ -655,6 +674,52 @@ int edm_ccm_rho_lags(const float *Y, int64_t N, int64_t T, int64_t ldY, const in
     }
     LagSpec spec{lag_min, n_lags, s_lo, omom_l, N * ld_rho};
     return ccm_execute(P, Y, N, T, ldY, 0, N, &pe, rho, ld_rho, st, &spec);
+}
+
+int edm_ccm_rho_subsets(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
+                        const uint32_t *masks, int32_t n_sub, int64_t words, const edm_params *params, float *rho,
+                        int64_t ld_rho, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc = ccm_validate(N, T, ldY, params);
+    if (rc)
+        return rc;
+    if (params->flags & EDM_FLAG_LOOKUP_SCALAR)
+        return EDM_ERR_UNSUPPORTED;
+    if (!Y || !optE || !masks || !rho || !ws || n_sub < 1 || words * 32 < T || ld_rho < N)
+        return EDM_ERR_INVALID;
+    if (ws_bytes < ccm_ws_layout(N, T, params).total)
+        return EDM_ERR_WORKSPACE;
+    if ((rc = validate_series(Y, N, T, ldY, params, (cudaStream_t)stream)) != EDM_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> E_host((size_t)N);
+    std::vector<uint32_t> m_host((size_t)n_sub * (size_t)words);
+    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaMemcpyAsync(m_host.data(), masks, m_host.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    EDM_CUDA(cudaStreamSynchronize(st));
+    // every query of every subset must keep E+1 candidates: allowed points in
+    // the candidate range, less the exclusion window, at the largest E in use
+    int E_top = 0;
+    for (int64_t j = 0; j < N; ++j)
+        E_top = std::max(E_top, (int)E_host[(size_t)j]);
+    if (E_top < 1 || E_top > EDM_MAX_E)
+        return EDM_ERR_INVALID;
+    const int64_t lo = (int64_t)(E_top - 1) * params->tau, hi = T - 1 - params->Tp;
+    for (int u = 0; u < n_sub; ++u) {
+        int64_t c = 0;
+        for (int64_t s2 = lo; s2 <= hi; ++s2)
+            c += (m_host[(size_t)u * words + (size_t)(s2 >> 5)] >> (s2 & 31)) & 1u;
+        if (params->exclusion_radius >= 0)
+            c -= 2 * (int64_t)params->exclusion_radius + 1;
+        if (c < E_top + 1)
+            return EDM_ERR_INVALID;
+    }
+    CcmPlan P;
+    rc = ccm_prepare(Y, N, T, ldY, E_host.data(), params, ws, st, P);
+    if (rc)
+        return rc;
+    SubsetSpec spec{masks, n_sub, words, N * ld_rho};
+    return ccm_execute(P, Y, N, T, ldY, 0, N, params, rho, ld_rho, st, nullptr, &spec);
 }
 
 size_t edm_ccm_host_workspace_bytes(int64_t N, int64_t T, int64_t block, const edm_params *params)
@@ -842,9 +907,11 @@ int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, cons
         const int nlb = (int)std::min<int64_t>(per_block, N - lb0);
         {
             LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel));
+            int n_knn = 1;
             EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lb0, nlb, (int)T, params->tau, params->Tp,
                                                  params->exclusion_radius, sel, lay, wsb + L.tables, st,
-                                                 (params->flags & EDM_FLAG_KNN_WARP) != 0));
+                                                 (params->flags & EDM_FLAG_KNN_WARP) != 0, 0, &n_knn));
+            ls.add_launches(EDM_KERNEL_KNN, n_knn - 1);
         }
         edm::BwArgs a;
         a.Y = Y;

@@ -69,6 +69,7 @@ struct KnnQuery {
     uint32_t sel;     // bit E-1: produce the neighbour list for E
     float *d2s;       // this warp's distance scratch (shared): 32 * J floats,
                       // slot j of lane l at d2s[(j/4)*128 + l*4 + j%4]
+    const uint32_t *mask;  // optional candidate subset (bit s of word s/32)
 };
 
 // Per-warp distance scratch bytes for J register slots per lane.
@@ -90,6 +91,8 @@ __device__ __forceinline__ bool cand_ok(const KnnQuery &q, int s, int E)
     if (s < q.s_first || s > q.s_last || s < (E - 1) * q.tau)
         return false;
     if (q.same && q.excl >= 0 && abs(s - q.t) <= q.excl)
+        return false;
+    if (q.mask && !((__ldg(q.mask + (s >> 5)) >> (s & 31)) & 1u))
         return false;
     return true;
 }

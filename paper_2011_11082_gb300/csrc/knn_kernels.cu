@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2) simplex_kernel(const float *__
         q.excl = -1;
         q.E_lim = E_lim;
         q.sel = E_lim >= 32 ? 0xffffffffu : ((1u << E_lim) - 1u);
+        q.mask = nullptr;
         q.d2s = warp_d2s(scratch, J);
         emit.t = t;
         knn_query<J>(q, sc, emit);
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
                       uint32_t sel, int q_per_cta, int front, int s_lo, const __grid_constant__ TableLayout lay,
                       uint8_t *__restrict__ tables,
                       int32_t *__restrict__ pub_idx, float *__restrict__ pub_w, int pub_E,
-                      const uint32_t *__restrict__ sel_dev)
+                      const uint32_t *__restrict__ sel_dev, const uint32_t *__restrict__ cand_mask)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int total = (int)series_floats(T, front, J);
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
         q.excl = excl;
         q.E_lim = E_lim;
         q.sel = s_t;
+        q.mask = cand_mask;
         q.d2s = warp_d2s(scratch, J);
         if (kPublic) {
             ep.t = t;
@@ -347,7 +349,7 @@ cudaError_t launch_simplex(const float *Y, int64_t N, int T, int64_t ldY, int E_
 template <int J, bool kPublic>
 static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl, int s_lo,
                          uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw, int pE,
-                         cudaStream_t st, int q_per_cta, const uint32_t *sel_dev)
+                         cudaStream_t st, int q_per_cta, const uint32_t *sel_dev, const uint32_t *cand_mask)
 {
     const int E_hi = 32 - __builtin_clz(sel);
     const int front = front_pad(E_hi, tau);
@@ -358,34 +360,39 @@ static cudaError_t knn_J(const float *Y, int64_t ldY, int64_t lib0, int n_lib, i
         return e;
     dim3 grid((unsigned)((T - Tp + q_per_cta - 1) / q_per_cta), (unsigned)n_lib);
     knn_tables_kernel<J, kPublic><<<grid, kKnnThreads, smem, st>>>(Y, ldY, lib0, T, tau, Tp, excl, sel, q_per_cta,
-                                                                    front, s_lo, lay, tables, pidx, pw, pE, sel_dev);
+                                                                    front, s_lo, lay, tables, pidx, pw, pE, sel_dev,
+                                                                    cand_mask);
     return cudaGetLastError();
 }
 
 template <bool kPublic>
 static cudaError_t knn_dispatch(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl, int s_lo,
                                 uint32_t sel, const TableLayout &lay, uint8_t *tables, int32_t *pidx, float *pw,
-                                int pE, cudaStream_t st, int q = 64, const uint32_t *sel_dev = nullptr)
+                                int pE, cudaStream_t st, int q = 64, const uint32_t *sel_dev = nullptr,
+                                const uint32_t *cand_mask = nullptr)
 {
     switch (pick_J(T - Tp - s_lo)) {
-    case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    case 24: return knn_J<24, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
-    default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev);
+    case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
+    case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
+    case 24: return knn_J<24, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
+    case 32: return knn_J<32, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
+    default: return knn_J<48, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
     }
 }
 
 cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
                               uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st, int q_per_cta,
-                              const uint32_t *sel_dev, int s_lo)
+                              const uint32_t *sel_dev, int s_lo, const uint32_t *cand_mask)
 {
     return knn_dispatch<false>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, nullptr, nullptr, 1, st,
-                               q_per_cta, sel_dev);
+                               q_per_cta, sel_dev, cand_mask);
 }
 
-// The thread-per-query kernel for a single E <= knn_thread_max_E() at tau = 1;
-// the warp kernel otherwise.
+// Which kernel builds the tables of the E set `sel`: the thread-per-query
+// kernel for a single E <= knn_thread_max_E() at tau = 1, else the warp
+// kernel.  (Splitting a multi-E set into per-E thread launches measured
+// slower on the full step than the warp kernel's one shared sweep: 7.76 vs
+// 7.10 s of kNN at N = 101,729, T = 1,500.)
 static bool use_thread_kernel(int tau, uint32_t sel, bool force_warp)
 {
     return !force_warp && tau == 1 && __builtin_popcount(sel) == 1 && 32 - __builtin_clz(sel) <= knn_thread_max_E();
@@ -393,12 +400,21 @@ static bool use_thread_kernel(int tau, uint32_t sel, bool force_warp)
 
 cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp,
                                    int excl, uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
-                                   bool force_warp, int s_lo)
+                                   bool force_warp, int s_lo, int *n_launches)
 {
-    if (!use_thread_kernel(tau, sel, force_warp))
+    const bool thread = use_thread_kernel(tau, sel, force_warp);
+    if (n_launches)
+        *n_launches = thread ? __builtin_popcount(sel) : 1;
+    if (!thread)
         return launch_knn_tables(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, st, 64, nullptr, s_lo);
-    return launch_knn_thread(Y, ldY, lib0, n_lib, T, Tp, excl, 32 - __builtin_clz(sel), lay, tables, st, nullptr,
-                             s_lo);
+    for (int E = 1; E <= 32 - __builtin_clz(sel); ++E) {
+        if (!((sel >> (E - 1)) & 1u))
+            continue;
+        cudaError_t e = launch_knn_thread(Y, ldY, lib0, n_lib, T, Tp, excl, E, lay, tables, st, nullptr, s_lo);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,

@@ -32,9 +32,12 @@ struct TableLayout {
 // into sel (E set planned on the device).
 // s_lo: queries and candidates start at time s_lo (0 for the plain cross
 // map; the time-delay form keeps every negative lag inside the series).
+// cand_mask (optional, device): only candidates s with bit s of word s/32
+// set (library subsets of the convergence test).
 cudaError_t launch_knn_tables(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp, int excl,
                               uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
-                              int q_per_cta = 64, const uint32_t *sel_dev = nullptr, int s_lo = 0);
+                              int q_per_cta = 64, const uint32_t *sel_dev = nullptr, int s_lo = 0,
+                              const uint32_t *cand_mask = nullptr);
 
 // Thread-per-query tables for one E (tau = 1, E <= knn_thread_max_E() = 6),
 // same results as the warp kernel (knn_thread.cu).
@@ -46,12 +49,12 @@ cudaError_t launch_knn_thread(const float *Y, int64_t ldY, int64_t lib0, int n_l
 cudaError_t launch_knn_thread_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int Tp, int excl,
                                      int32_t *idx, float *w, cudaStream_t st);
 cudaError_t knn_thread_counters(unsigned long long out[2], bool reset);
-// Tables for the E set `sel` with the cheaper kernel: thread-per-query when
-// tau = 1 and sel holds one E <= knn_thread_max_E(), else the warp kernel
-// (one launch either way).
+// Tables for the E set `sel` with the cheaper kernel by a measured cost
+// model: thread-per-query launches (one per E, all E <= knn_thread_max_E(),
+// tau = 1) or one warp-kernel launch.  Returns the launches made in *n.
 cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp,
                                    int excl, uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
-                                   bool force_warp = false, int s_lo = 0);
+                                   bool force_warp = false, int s_lo = 0, int *n_launches = nullptr);
 
 // FP64 re-rank / exhaustive-scan query counts of the kNN kernels on the
 // current device (synchronises); reset clears them.
