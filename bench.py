@@ -276,6 +276,64 @@ def bench_batched(args, lib, edm, _abi, torch, edm_synth):
     return 0
 
 
+# The paper's dataset-size study (Sec. IV, "Impact of Dataset Size"): runtime
+# and its split between kNN and lookup while the number of series grows at
+# 10,000 time steps, and while the number of time steps grows at 1,000
+# series (up to 40,000).  Synthetic coupled maps stand in for its dummy
+# datasets; the coupling density keeps about 10 inputs per map.
+SWEEPS = {
+    "series": [(n, 10000) for n in (500, 1000, 2000, 4000, 8000)],
+    "steps": [(1000, t) for t in (1000, 2000, 5000, 10000, 20000, 40000)],
+}
+
+
+def bench_sweep(args, lib, edm, _abi, torch, edm_synth):
+    """One JSON line per (N, T) of the sweep: step time (both phases, CUDA
+    events), pairs/s and the per-kernel split from per-launch events."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    E_max = 20
+    for N, T in SWEEPS[args.sweep]:
+        Y = edm_synth.coupled_logistic(N, T, min(0.05, 10.0 / N), 0.02, seed_data=0, seed_noise=1)
+        Yd = torch.from_numpy(Y).to(dev)
+        rho = torch.empty((N, N), dtype=torch.float32, device=dev)
+        ws = torch.empty(edm.edm_ccm_workspace_bytes(N, T), dtype=torch.uint8, device=dev)
+
+        def step():
+            optE, _ = edm.edm_optimal_E(Yd, E_max=E_max, return_rho=False)
+            edm.edm_ccm_rho(Yd, optE, out=rho, workspace=ws)
+            return optE
+
+        optE = step()  # warm-up
+        torch.cuda.synchronize()
+        lib.edm_profile_enable(1)
+        for k in range(4):
+            lib.edm_profile_read(k, None, None, None)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            optE = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        lib.edm_profile_enable(0)
+        ms = ev0.elapsed_time(ev1) / args.steps
+        split = {}
+        for k in range(4):
+            m, n, u = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+            lib.edm_profile_read(k, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
+            split[_abi.KERNEL_NAMES[k]] = round(m.value / args.steps, 3)
+        hist = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:].tolist()
+        line = {"sweep": args.sweep, "N": N, "T": T, "ms_per_step": ms, "pairs_per_s": float(N) * N / (ms / 1e3),
+                "steps": args.steps, "warmup": 1, "kernels_ms": split,
+                "lookup_tiles": "global/L2" if T > 3103 else "shared memory", "optE_histogram": hist,
+                "data": "synthetic coupled logistic maps, density min(5%, 10/N), b_max 0.02"}
+        print(json.dumps(line), flush=True)
+        del Yd, rho, ws
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,6 +349,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=0, help="library rows the oracle times (0: 2 x cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
+                    help="dataset-size sweep (one JSON line per size) instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -316,6 +376,8 @@ def main():
     lib = _abi.load()
     if args.workload == BATCHED:
         return bench_batched(args, lib, edm, _abi, torch, edm_synth)
+    if args.sweep:
+        return bench_sweep(args, lib, edm, _abi, torch, edm_synth)
 
     N, T, dens, bmax, E_max = WORKLOADS[args.workload]
     # independent problems per rank (weak scaling): rank r uses data seed r

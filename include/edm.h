@@ -42,14 +42,18 @@ extern "C" {
 
 /* Largest embedding dimension the kernels are built for. */
 #define EDM_MAX_E 20
-/* Longest series the kernels accept (indices are kept in 16 bits). */
+/* Upper bound on the series length (indices are kept in 16 bits).  The kNN
+   kernels stage a whole series in shared memory, which lowers the practical
+   limit to about 46,000 steps: longer series return EDM_ERR_UNSUPPORTED. */
 #define EDM_MAX_T 65535
 
 #define EDM_PRECISION_FP32 0         /* targets staged as float32 */
 #define EDM_PRECISION_FP16_TARGETS 1 /* targets staged as float16 (for E <= 11; larger
                                         E stay float32); the FP32 table weights enter
                                         each FMA as float16 copies; exact products,
-                                        FP32 accumulation */
+                                        FP32 accumulation.  Series longer than about
+                                        3,100 steps (target tiles read from L2, not
+                                        shared memory) always stage float32 */
 
 /* flags */
 #define EDM_FLAG_NONE 0u
@@ -76,7 +80,7 @@ typedef struct edm_params {
 } edm_params;
 
 /*
- * Phase 1, simplex projection (Algorithm 1 lines 1-11; Sec. II-B).
+ * Phase 1, simplex projection (Algorithm 1, its simplex phase; Sec. II-B).
  * For every series i: library = first floor(T/2) samples, target = the rest,
  * both embedded within themselves with lags (0, tau, .., (E-1)tau) counted
  * backwards; each target point's E+1 nearest library points (ascending
@@ -94,7 +98,7 @@ int edm_optimal_E(const float *Y, int64_t N, int64_t T, int64_t ldY, const edm_p
                   int32_t *optE, float *rho_by_E, void *stream);
 
 /*
- * Phase 2 kNN tables (Algorithm 2 lines 4-6, Algorithms 3/4; the table
+ * Phase 2 kNN tables (Algorithm 2, its kNN step; Algorithms 3/4; the table
  * reuse of Sec. III-B).  For each of n_lib library series and one E: every
  * embedded point t in [(E-1)tau, T-1-Tp] (row r = t-(E-1)tau) gets its E+1
  * nearest embedded points s of the same series in the same range
@@ -110,7 +114,7 @@ int edm_knn_table(const float *Y, int64_t n_lib, int64_t T, int64_t ldY, int32_t
                   const edm_params *params, int32_t *idx, float *w, int64_t Tq, void *stream);
 
 /*
- * Phase 2 cross map (Algorithm 2 lines 8-11; Algorithm 5 lookup; corrcoef).
+ * Phase 2 cross map (Algorithm 2, its lookup and corrcoef steps; Algorithm 5).
  * For libraries i in [lib_begin, lib_begin+lib_count) and every target j:
  * prediction p(t) = sum_n w[t,n] y_j(s_n+Tp) with library i's table at
  * E = optE[j], observation o(t) = y_j(t+Tp), rho(i,j) = Pearson(o, p).
@@ -122,6 +126,10 @@ int edm_knn_table(const float *Y, int64_t n_lib, int64_t T, int64_t ldY, int32_t
  *   ws     device workspace of at least edm_ccm_workspace_bytes(N, T, params)
  * This call synchronises `stream` once, to read optE on the host and plan
  * the target grouping; everything else is enqueued asynchronously.
+ * Targets are staged in tiles of 32 (64 FP16) series; up to about 3,100
+ * steps a tile sits in shared memory during the lookup, longer series (the
+ * time-step sweep of the paper's Sec. IV reaches 40,000) read their tiles
+ * from global memory / L2 with the same results up to summation order.
  */
 int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
                 int64_t lib_begin, int64_t lib_count, const edm_params *params,

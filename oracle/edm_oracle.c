@@ -19,7 +19,7 @@
  *     and the text of Sec. III-B (nearest = ascending distance; ties go to
  *     the smaller candidate index);
  *   - normalize: distances to exponential scale, each row normalised,
- *     Algorithm 1 line "normalize"; weights u_n = exp(-d_n / d_1), w = u/sum(u)
+ *     the normalisation step of Algorithm 1; weights u_n = exp(-d_n / d_1), w = u/sum(u)
  *     with d_1 the nearest distance; when d_1 = 0 only exact duplicates
  *     (d_n = 0) carry weight;
  *   - lookup: prediction(t) = sum_n w[t,n] * y(s_n + Tp), Algorithm 5, one

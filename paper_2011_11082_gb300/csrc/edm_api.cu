@@ -119,6 +119,11 @@ constexpr size_t kTileBlockBytes = 64ull << 20;  // target tiles per block
 constexpr size_t kTableBytes = 48ull << 20;      // kNN tables per library block (L2 target)
 constexpr int64_t kMinLibBlock = 256;            // library block floor
 
+// Library block floor for series of length T: long series give every
+// library thousands of kNN queries, so fewer libraries fill the GPU and the
+// floor shrinks with T (keeping the table area near 1.4 GB at most).
+int64_t min_lib_block(int64_t T) { return T <= 4096 ? kMinLibBlock : std::max<int64_t>(16, kMinLibBlock * 4096 / T); }
+
 int tq_pad(int64_t T, const edm_params *p) { return (int)(((T - p->Tp) + 31) / 32 * 32); }
 
 edm::TableLayout make_layout(uint32_t sel, int64_t T, const edm_params *p)
@@ -176,7 +181,7 @@ CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
     w.tables = off;
     edm::TableLayout all = make_layout((1u << EDM_MAX_E) - 1u, T, p);
     w.table_bytes = std::max(kTableBytes, (size_t)all.lib_stride);
-    w.table_cap = std::max(w.table_bytes, (size_t)std::min<int64_t>(N, kMinLibBlock) * (size_t)all.lib_stride);
+    w.table_cap = std::max(w.table_bytes, (size_t)std::min<int64_t>(N, min_lib_block(T)) * (size_t)all.lib_stride);
     off += align256(w.table_cap);
     w.total = off;
     return w;
@@ -381,6 +386,7 @@ struct CcmPlan {
     float *tiles_d;
     uint8_t *tables_d;
     bool want_f16, scalar;
+    bool l2;  // long series: tiles stay in global memory (FP32 only)
     int RB;
     CcmWs L;
 };
@@ -397,7 +403,7 @@ int ccm_validate(int64_t N, int64_t T, int64_t ldY, const edm_params *params)
     const bool scalar = (params->flags & EDM_FLAG_LOOKUP_SCALAR) != 0;
     if (scalar && params->precision != EDM_PRECISION_FP32)
         return EDM_ERR_INVALID;
-    if (T > edm::knn_max_T() || (scalar ? edm::lookup_smem_bytes((int)T) > 227u * 1024u : edm::chunked_row_bytes((int)T) == 0))
+    if (T > edm::knn_max_T() || (scalar && edm::lookup_smem_bytes((int)T) > 227u * 1024u))
         return EDM_ERR_UNSUPPORTED;
     return EDM_OK;
 }
@@ -410,6 +416,7 @@ int ccm_prepare(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
     const CcmWs &L = P.L;
     P.scalar = (params->flags & EDM_FLAG_LOOKUP_SCALAR) != 0;
     P.RB = ccm_row_bytes(T, params);
+    P.l2 = !P.scalar && edm::lookup_needs_l2((int)T);
     int64_t count[EDM_MAX_E + 2] = {0};
     for (int64_t j = 0; j < N; ++j) {
         int E = E_host[(size_t)j];
@@ -428,7 +435,7 @@ int ccm_prepare(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
             pi[(size_t)fill[E_host[(size_t)j]]++] = (int32_t)j;
     }
     P.tiles.clear();
-    P.want_f16 = params->precision == EDM_PRECISION_FP16_TARGETS;
+    P.want_f16 = params->precision == EDM_PRECISION_FP16_TARGETS && !P.l2;
     for (int E = 1; E <= EDM_MAX_E; ++E) {
         const bool f16 = P.want_f16 && E + 1 <= edm::kF16MaxK;
         const int width = f16 ? P.RB / 2 : P.RB / 4;
@@ -506,7 +513,7 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
         // L2-sized library blocks; blocks of rare-E target blocks (many E,
         // few tiles) may spill to HBM rather than shrink below kMinLibBlock
         const int64_t per_block = std::min<int64_t>(
-            65535, std::max<int64_t>(std::min<int64_t>(kMinLibBlock, (int64_t)(L.table_cap / (size_t)lay.lib_stride)),
+            65535, std::max<int64_t>(std::min<int64_t>(min_lib_block(T), (int64_t)(L.table_cap / (size_t)lay.lib_stride)),
                                      (int64_t)(L.table_bytes / (size_t)lay.lib_stride)));
         for (int64_t lb0 = 0; lb0 < lib_count; lb0 += per_block)
           for (int su = 0; su < (subsets ? subsets->n_sub : 1); ++su) {
@@ -574,7 +581,10 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
                         a.rho = rho + li * lags->rho_stride;
                     }
                     LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                    EDM_CUDA(edm::launch_lookup_multi(a, P.RB, st));
+                    if (P.l2)
+                        EDM_CUDA(edm::launch_lookup_l2(a, st));
+                    else
+                        EDM_CUDA(edm::launch_lookup_multi(a, P.RB, st));
                 }
             }
         }

@@ -33,10 +33,26 @@ static size_t knn_smem_bytes_exact(int T, int front, int J)
            (size_t)kKnnWarps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(J)) + 64;
 }
 
+// Dynamic shared memory a kNN CTA may take (the simplex kernel also holds
+// about 7 KB of static reductions; 227 KB is the per-CTA limit).
+constexpr size_t kKnnSmemCap = 216 * 1024;
+
+// Register slots per lane: the preferred J for the candidate count, lowered
+// (more, shorter candidate chunks) while the staged series and the per-warp
+// scratch would not fit kKnnSmemCap -- long series (T beyond about 30,000).
+static int fit_J(int J, int T, int front)
+{
+    while (J > 8 && knn_smem_bytes_exact(T, front, J) > kKnnSmemCap)
+        J = J == 48 ? 32 : J - 8;
+    return J;
+}
+
 int knn_max_T()
 {
-    return (int)((200 * 1024 - kKnnWarps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(48)) - 64) / sizeof(float)) -
-           32 * 48 - 1024;
+    // J = 8, front for E = EDM_MAX_E at tau = 1
+    const size_t fixed = (size_t)kKnnWarps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(8)) + 64;
+    const size_t floats = (kKnnSmemCap - fixed) / sizeof(float);
+    return (int)(floats - (size_t)front_pad(EDM_MAX_E, 1) - 32 * 8 - 4 - 4);
 }
 
 // Distance scratch of warp w (behind the per-warp KnnWarpScratch array).
@@ -337,7 +353,7 @@ cudaError_t launch_simplex(const float *Y, int64_t N, int T, int64_t ldY, int E_
                            float *rho_by_E, cudaStream_t st)
 {
     const int h = T / 2;
-    switch (pick_J(h - Tp)) {
+    switch (fit_J(pick_J(h - Tp), T, front_pad(E_max, tau))) {
     case 8: return simplex_J<8>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
     case 16: return simplex_J<16>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
     case 24: return simplex_J<24>(Y, N, T, ldY, E_max, tau, Tp, optE, rho_by_E, st);
@@ -371,7 +387,7 @@ static cudaError_t knn_dispatch(const float *Y, int64_t ldY, int64_t lib0, int n
                                 int pE, cudaStream_t st, int q = 64, const uint32_t *sel_dev = nullptr,
                                 const uint32_t *cand_mask = nullptr)
 {
-    switch (pick_J(T - Tp - s_lo)) {
+    switch (fit_J(pick_J(T - Tp - s_lo), T, front_pad(32 - __builtin_clz(sel), tau))) {
     case 8: return knn_J<8, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
     case 16: return knn_J<16, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);
     case 24: return knn_J<24, kPublic>(Y, ldY, lib0, n_lib, T, tau, Tp, excl, s_lo, sel, lay, tables, pidx, pw, pE, st, q, sel_dev, cand_mask);

@@ -119,6 +119,10 @@ size_t chunked_smem_bytes(int T, int RB);
 int chunked_row_bytes(int T);
 // Tiles of any E / format in one launch (each CTA runs its tile's variant).
 cudaError_t launch_lookup_multi(const LookupArgs &a, int RB, cudaStream_t st);
+// Tiles too long for shared memory (T beyond about 3,500): FP32 tiles of
+// 128-byte rows read from global memory / L2 (lookup_l2.cu).
+bool lookup_needs_l2(int T);
+cudaError_t launch_lookup_l2(const LookupArgs &a, cudaStream_t st);
 cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
                                     const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st,
                                     int RB = 128);
