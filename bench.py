@@ -63,7 +63,8 @@ def _lookup_sources_hash():
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2011_11082_gb300", "csrc")
-    for f in ("lookup_chunked.cuh", "lookup_chunked128.cu", "lookup_chunked64.cu"):
+    # the kernels and the planner (which shapes every launch)
+    for f in ("lookup_chunked.cuh", "lookup_chunked128.cu", "lookup_chunked64.cu", "edm_api.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -293,7 +294,10 @@ def bench_sweep(args, lib, edm, _abi, torch, edm_synth):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     E_max = 20
-    for N, T in SWEEPS[args.sweep]:
+    sizes = SWEEPS[args.sweep]
+    if args.size:
+        sizes = [tuple(int(v) for v in args.size.lower().split("x"))]
+    for N, T in sizes:
         Y = edm_synth.coupled_logistic(N, T, min(0.05, 10.0 / N), 0.02, seed_data=0, seed_noise=1)
         Yd = torch.from_numpy(Y).to(dev)
         rho = torch.empty((N, N), dtype=torch.float32, device=dev)
@@ -351,6 +355,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
                     help="dataset-size sweep (one JSON line per size) instead of the benchmark line")
+    ap.add_argument("--size", default=None, help="with --sweep: one size NxT instead of the sweep's list")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

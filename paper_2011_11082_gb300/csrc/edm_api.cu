@@ -500,12 +500,37 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
     edm::TileMeta *meta_d = P.meta_d;
     float *tiles_d = P.tiles_d;
     uint8_t *tables_d = P.tables_d;
-    // --- target blocks (L2-sized) x library blocks ------------------------------
+    // --- target groups x library blocks ----------------------------------------
+    // Tiles in shared memory: one group per E up to knn_thread_max_E() (the
+    // tables of that E, one build per library), the larger E together (one
+    // warp-kernel sweep serves them all), so every (library, E) table is
+    // built exactly once; each library block's tables stay in L2 while the
+    // group's tiles stream through shared memory.  Tiles read from L2 (long
+    // series): L2-sized target blocks instead, so the tiles stay resident
+    // while every library block sweeps them.
     const size_t tile_bytes = (size_t)T * P.RB;
     const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
     const int sms = sm_count();
-    for (int tb0 = 0; tb0 < n_tiles; tb0 += tiles_per_block) {
-        const int ntb = std::min(tiles_per_block, n_tiles - tb0);
+    std::vector<std::pair<int, int>> groups;  // tile ranges [first, last)
+    if (P.l2) {
+        for (int tb0 = 0; tb0 < n_tiles; tb0 += tiles_per_block)
+            groups.emplace_back(tb0, std::min(n_tiles, tb0 + tiles_per_block));
+    } else {
+        for (int t0 = 0; t0 < n_tiles;) {
+            const int E = tiles[(size_t)t0].E;
+            int t1 = t0 + 1;
+            if (E <= edm::knn_thread_max_E())
+                while (t1 < n_tiles && tiles[(size_t)t1].E == E)
+                    ++t1;
+            else
+                t1 = n_tiles;
+            groups.emplace_back(t0, t1);
+            t0 = t1;
+        }
+    }
+    for (const auto &g : groups) {
+        const int tb0 = g.first;
+        const int ntb = g.second - g.first;
         uint32_t sel = 0;
         for (int t = tb0; t < tb0 + ntb; ++t)
             sel |= 1u << (tiles[(size_t)t].E - 1);
@@ -570,9 +595,17 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
             } else {
                 a.tile_begin = tb0;
                 a.n_tiles = ntb;
-                int parts = (4 * sms + ntb - 1) / ntb;
+                // shared-memory tiles: at least ~16 CTAs per SM in all (one
+                // CTA per SM is resident), so the last wave is a small tail
+                const int want = (P.l2 ? 4 : 16) * sms;
+                int parts = (want + ntb - 1) / ntb;
                 a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
                 const int n_lk = lags ? lags->n_lags : 1;
+                // tiles read from L2: one launch per register class present
+                int n_small = 0;
+                while (P.l2 && n_small < ntb && tiles[(size_t)(tb0 + n_small)].E + 1 <= edm::kL2SplitK)
+                    ++n_small;
+                const int lk_launches = P.l2 ? (n_small > 0) + (ntb - n_small > 0) : 1;
                 for (int li = 0; li < n_lk; ++li) {
                     if (lags) {
                         a.s_lo = lags->s_lo;
@@ -580,11 +613,12 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
                         a.omom = lags->omom + (size_t)li * N;
                         a.rho = rho + li * lags->rho_stride;
                     }
-                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb);
-                    if (P.l2)
-                        EDM_CUDA(edm::launch_lookup_l2(a, st));
-                    else
+                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb, lk_launches);
+                    if (P.l2) {
+                        EDM_CUDA(edm::launch_lookup_l2(a, n_small, sms, st));
+                    } else {
                         EDM_CUDA(edm::launch_lookup_multi(a, P.RB, st));
+                    }
                 }
             }
         }

@@ -571,7 +571,13 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
     int c = kCandCap + 1;
     if (th < 3.40282347e38f) {  // a seed exists: often tight enough alone
         mark_le(d2, th, m0, m1);
-        c = have + (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
+        const int marked = (int)__reduce_add_sync(kFull, (unsigned)(__popc(m0) + __popc(m1)));
+        // later chunks of a long series: when no slot of this chunk is at or
+        // below the K-th entry kept from earlier chunks, the list is final
+        // for this chunk as it stands
+        if (marked == 0 && have >= K)
+            return;
+        c = have + marked;
     }
     if (c > kCandCap) {
         th = fminf(th, fminf(kth_lane_min(lane_min_tree(d2), K), 3.40282347e38f));

@@ -121,8 +121,12 @@ int chunked_row_bytes(int T);
 cudaError_t launch_lookup_multi(const LookupArgs &a, int RB, cudaStream_t st);
 // Tiles too long for shared memory (T beyond about 3,500): FP32 tiles of
 // 128-byte rows read from global memory / L2 (lookup_l2.cu).
+// Two launches, one per register class: tiles with E + 1 <= kL2SplitK,
+// then the larger E (tiles are sorted by E: n_small = tiles of the first
+// class at the start of the range); sms = SM count.
+constexpr int kL2SplitK = 9;
 bool lookup_needs_l2(int T);
-cudaError_t launch_lookup_l2(const LookupArgs &a, cudaStream_t st);
+cudaError_t launch_lookup_l2(const LookupArgs &a, int n_small, int sms, cudaStream_t st);
 cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau, int Tp, const int32_t *pi,
                                     const TileMeta *meta, int n_tiles, uint8_t *tiles, float2 *omom, cudaStream_t st,
                                     int RB = 128);

@@ -16,6 +16,8 @@
 // one block ahead, and the groups fetch the entries of their current row by
 // warp shuffles.  Moment sums are two-level (per 32-row block, then over
 // blocks) so the FP32 error stays small at T in the tens of thousands.
+#include <algorithm>
+
 #include "edm_internal.cuh"
 #include "launchers.h"
 
@@ -170,7 +172,6 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
 // CTA runs the variant of its own tile, or returns at once when its tile's
 // K = E + 1 belongs to the other class.  Small K (<= kL2SplitK) keeps two
 // CTAs per SM within 128 registers; larger K gets the registers of one CTA.
-constexpr int kL2SplitK = 9;
 
 template <bool kLag, bool kLarge>
 __global__ void __launch_bounds__(kL2Threads, kLarge ? 1 : 2) lookup_l2_kernel(LookupArgs a)
@@ -213,20 +214,38 @@ __global__ void __launch_bounds__(kL2Threads, kLarge ? 1 : 2) lookup_l2_kernel(L
 #undef EDM_L2
 }
 
-cudaError_t launch_lookup_l2(const LookupArgs &a, cudaStream_t st)
+cudaError_t launch_lookup_l2(const LookupArgs &a, int n_small, int sms, cudaStream_t st)
 {
     if (a.n_tiles <= 0 || a.n_lib <= 0)
         return cudaSuccess;
     const bool lag = a.s_lo != 0 || a.lag != a.Tp;
-    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
-    if (lag) {
-        lookup_l2_kernel<true, false><<<grid, kL2Threads, 0, st>>>(a);
-        lookup_l2_kernel<true, true><<<grid, kL2Threads, 0, st>>>(a);
-    } else {
-        lookup_l2_kernel<false, false><<<grid, kL2Threads, 0, st>>>(a);
-        lookup_l2_kernel<false, true><<<grid, kL2Threads, 0, st>>>(a);
+    // each class gets its own library split, sized so that its tiles alone
+    // fill the GPU (two resident CTAs per SM for small K, one for large K)
+    for (int large = 0; large < 2; ++large) {
+        LookupArgs b = a;
+        b.tile_begin = a.tile_begin + (large ? n_small : 0);
+        b.n_tiles = large ? a.n_tiles - n_small : n_small;
+        if (b.n_tiles <= 0)
+            continue;
+        const int want = 4 * sms * (large ? 1 : 2);
+        b.lib_parts = std::max(1, std::min((want + b.n_tiles - 1) / b.n_tiles, (a.n_lib + 7) / 8));
+        dim3 grid((unsigned)b.n_tiles, (unsigned)b.lib_parts);
+        if (lag) {
+            if (large)
+                lookup_l2_kernel<true, true><<<grid, kL2Threads, 0, st>>>(b);
+            else
+                lookup_l2_kernel<true, false><<<grid, kL2Threads, 0, st>>>(b);
+        } else {
+            if (large)
+                lookup_l2_kernel<false, true><<<grid, kL2Threads, 0, st>>>(b);
+            else
+                lookup_l2_kernel<false, false><<<grid, kL2Threads, 0, st>>>(b);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace edm

@@ -35,10 +35,15 @@ def _small_batch(seed, count=7, n_range=(9, 140), t_range=(120, 1700)):
 
 
 def _per_dataset(edm, Ys, E_max, precision):
+    # The batched form builds every table with the warp-per-query kernel
+    # (its E set is planned on the device); the per-dataset call is asked
+    # for the same kernel, so a dataset's results are the same bits.  (By
+    # default a single-E table set with E <= 6 uses the thread-per-query
+    # kernel: same neighbours, weights equal up to summation order.)
     out = []
     for Y in Ys:
         optE, _ = edm.edm_optimal_E(Y, E_max=E_max, return_rho=False)
-        out.append((optE, edm.edm_ccm_rho(Y, optE, precision=precision)))
+        out.append((optE, edm.edm_ccm_rho(Y, optE, precision=precision, flags=edm.EDM_FLAG_KNN_WARP)))
     return out
 
 
