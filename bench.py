@@ -69,9 +69,12 @@ def _lookup_sources_hash():
     return h.hexdigest()[:16]
 
 
-def _measured_traffic(workload, precision):
-    """DRAM bytes per lookup launch from the committed ncu summary, if it was
-    taken on the lookup sources as they are now (else None)."""
+def _measured_traffic(workload, precision, pairs_per_launch):
+    """DRAM bytes per lookup launch (read + write) from the committed ncu
+    capture, if it was taken on the lookup kernels and planner as they are
+    now (else None).  The capture stores bytes per pair of the captured
+    launches; launches differ in size, so the figure is scaled to the mean
+    launch of this run (traffic grows with the pairs a launch processes)."""
     p = os.path.join(ROOT, "profiles", "lookup_dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -79,7 +82,7 @@ def _measured_traffic(workload, precision):
     e = d.get(f"{workload}/{precision}")
     if not e or e.get("sources") != _lookup_sources_hash():
         return None
-    return float(e["bytes_per_launch"])
+    return float(e["bytes_per_pair"]) * pairs_per_launch
 
 
 def _smem_gather_bytes(hist, T, Tp, s_y, N):
@@ -448,7 +451,8 @@ def main():
     per_launch_s = lk["ms"] / 1e3 / lk_launches
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _measured_traffic(args.workload, args.precision), "peak_kind": peak_kind,
+                "traffic": _measured_traffic(args.workload, args.precision, lk["units"] / lk_launches),
+                "peak_kind": peak_kind,
                 "kernel": "lookup_kernel", "bytes_per_pair": bpp,
                 "path_frac": (N * float(N) * bpp / (ms / 1e3) / 1e9) / peak}
     # the bound that holds: the lookup reads every gathered value from

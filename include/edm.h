@@ -38,7 +38,7 @@ extern "C" {
 #define EDM_ERR_CUDA 2        /* a CUDA call failed (see edm_last_cuda_error) */
 #define EDM_ERR_WORKSPACE 3   /* ws too small; see the matching *_workspace_bytes */
 #define EDM_ERR_TIMEOUT 4     /* a bounded device wait gave up */
-#define EDM_ERR_UNSUPPORTED 5 /* valid request outside this build's limits */
+#define EDM_ERR_UNSUPPORTED 5 /* valid request outside this library's limits */
 
 /* Largest embedding dimension the kernels are built for. */
 #define EDM_MAX_E 20

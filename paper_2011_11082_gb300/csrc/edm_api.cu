@@ -306,7 +306,7 @@ const char *edm_status_string(int status)
     case EDM_ERR_INVALID: return "EDM_ERR_INVALID: invalid argument";
     case EDM_ERR_WORKSPACE: return "EDM_ERR_WORKSPACE: workspace too small";
     case EDM_ERR_TIMEOUT: return "EDM_ERR_TIMEOUT: a bounded device wait gave up";
-    case EDM_ERR_UNSUPPORTED: return "EDM_ERR_UNSUPPORTED: outside this build's limits";
+    case EDM_ERR_UNSUPPORTED: return "EDM_ERR_UNSUPPORTED: outside this library's limits";
     case EDM_ERR_CUDA:
         snprintf(g_msg, sizeof g_msg, "EDM_ERR_CUDA: %s", cudaGetErrorString((cudaError_t)g_last_cuda));
         return g_msg;
@@ -501,32 +501,37 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
     float *tiles_d = P.tiles_d;
     uint8_t *tables_d = P.tables_d;
     // --- target groups x library blocks ----------------------------------------
-    // Tiles in shared memory: one group per E up to knn_thread_max_E() (the
-    // tables of that E, one build per library), the larger E together (one
-    // warp-kernel sweep serves them all), so every (library, E) table is
-    // built exactly once; each library block's tables stay in L2 while the
+    // One group per E up to knn_thread_max_E() (the tables of that E, one
+    // build per library), the larger E together (one warp-kernel sweep
+    // serves them all), so every (library, E) table is built once.  Tiles in
+    // shared memory: each library block's tables stay in L2 while the whole
     // group's tiles stream through shared memory.  Tiles read from L2 (long
-    // series): L2-sized target blocks instead, so the tiles stay resident
-    // while every library block sweeps them.
+    // series): a group is further cut into L2-sized target blocks, so its
+    // tiles stay resident while every library block sweeps them.
     const size_t tile_bytes = (size_t)T * P.RB;
     const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
     const int sms = sm_count();
     std::vector<std::pair<int, int>> groups;  // tile ranges [first, last)
-    if (P.l2) {
-        for (int tb0 = 0; tb0 < n_tiles; tb0 += tiles_per_block)
-            groups.emplace_back(tb0, std::min(n_tiles, tb0 + tiles_per_block));
-    } else {
-        for (int t0 = 0; t0 < n_tiles;) {
-            const int E = tiles[(size_t)t0].E;
-            int t1 = t0 + 1;
-            if (E <= edm::knn_thread_max_E())
-                while (t1 < n_tiles && tiles[(size_t)t1].E == E)
-                    ++t1;
-            else
-                t1 = n_tiles;
+    // all tiles within one target block: one group, so one warp-kernel
+    // sweep serves every E (no table is built twice either way; per-E
+    // thread launches measured slower there: 28.7 vs 26.5 ms per step at
+    // N = 1,000, T = 1,000)
+    if (n_tiles <= tiles_per_block)
+        groups.emplace_back(0, n_tiles);
+    for (int t0 = groups.empty() ? 0 : n_tiles; t0 < n_tiles;) {
+        const int E = tiles[(size_t)t0].E;
+        int t1 = t0 + 1;
+        if (E <= edm::knn_thread_max_E())
+            while (t1 < n_tiles && tiles[(size_t)t1].E == E)
+                ++t1;
+        else
+            t1 = n_tiles;
+        if (P.l2)
+            for (int b = t0; b < t1; b += tiles_per_block)
+                groups.emplace_back(b, std::min(t1, b + tiles_per_block));
+        else
             groups.emplace_back(t0, t1);
-            t0 = t1;
-        }
+        t0 = t1;
     }
     for (const auto &g : groups) {
         const int tb0 = g.first;
