@@ -331,10 +331,18 @@ def bench_sweep(args, lib, edm, _abi, torch, edm_synth):
             lib.edm_profile_read(k, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
             split[_abi.KERNEL_NAMES[k]] = round(m.value / args.steps, 3)
         hist = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:].tolist()
-        line = {"sweep": args.sweep, "N": N, "T": T, "ms_per_step": ms, "pairs_per_s": float(N) * N / (ms / 1e3),
+        value = float(N) * N / (ms / 1e3)
+        line = {"sweep": args.sweep, "N": N, "T": T, "ms_per_step": ms, "pairs_per_s": value,
                 "steps": args.steps, "warmup": 1, "kernels_ms": split,
                 "lookup_tiles": "global/L2" if T > 3103 else "shared memory", "optE_histogram": hist,
                 "data": "synthetic coupled logistic maps, density min(5%, 10/N), b_max 0.02"}
+        # the paper's GPU-over-CPU comparison along T: the FP64 oracle on the
+        # host cores (bounded sample, extrapolated), up to 10,000 steps (a
+        # longer series takes minutes of CPU time per point)
+        if args.sweep == "steps" and T <= 10000 and not args.no_cpu:
+            cb = cpu_baseline(Y, optE.cpu().numpy(), args.cpu_rows, N, E_max)
+            line["cpu_baseline"] = cb
+            line["speedup_vs_cpu"] = value / cb["value"]
         print(json.dumps(line), flush=True)
         del Yd, rho, ws
         torch.cuda.empty_cache()
