@@ -19,14 +19,6 @@ __host__ __device__ static size_t series_floats(int T, int front, int J) { retur
 
 // Shared memory: the padded series, then per warp a KnnWarpScratch, then
 // per warp the distance scratch of 32 * J floats.
-size_t knn_smem_bytes(int T, int warps)
-{
-    // worst case: J = 48, front for E = EDM_MAX_E at tau = 1 (larger tau is
-    // sized at launch)
-    return series_floats(T, front_pad(EDM_MAX_E, 1), 48) * sizeof(float) +
-           (size_t)warps * (sizeof(KnnWarpScratch) + knn_d2s_bytes(48)) + 64;
-}
-
 static size_t knn_smem_bytes_exact(int T, int front, int J)
 {
     return series_floats(T, front, J) * sizeof(float) +

@@ -9,8 +9,6 @@
 
 namespace edm {
 
-// Shared-memory bytes of the staged series plus per-warp kNN scratch.
-size_t knn_smem_bytes(int T, int warps);
 // Largest T the kNN kernels can stage in shared memory.
 int knn_max_T();
 
