@@ -207,7 +207,8 @@ size_t edm_ccm_host_workspace_bytes(int64_t N, int64_t T, int64_t block, const e
  *                     edm_ccm_rho: rho[j*ld_rho + i] = rho(library i -> target j)
  *   ws        device workspace of edm_ccm_rho_batched_workspace_bytes(...)
  * Each dataset needs the edm_optimal_E length condition for params->E_max,
- * N <= 65535, and T within what edm_ccm_rho accepts; the E grouping of its
+ * N <= 65535, and T short enough for a target tile to sit in shared memory
+ * (about 3,100 steps; longer series return EDM_ERR_UNSUPPORTED); the E grouping of its
  * targets is planned on the device, so the call never synchronises with
  * the GPU after its first use.
  * First call with a given (sets, params, ws, ws_bytes): the library times
@@ -273,7 +274,9 @@ size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *
  *   - Problems whose scratch exceeds the array (target tiles of about
  *     N*T*4 bytes plus the kNN tables of at least one library) return
  *     EDM_ERR_WORKSPACE before touching the device; e.g. N = 2,048 and
- *     T = 1,500 fit, N = 16,384 and T = 1,500 do not.
+ *     T = 1,500 fit, N = 16,384 and T = 1,500 do not.  Series longer than
+ *     a shared-memory target tile allows (about 3,100 steps) return
+ *     EDM_ERR_UNSUPPORTED.
  *   - The first call on each device resolves the array's device address
  *     (cudaGetSymbolAddress, that device current); make that first call
  *     before any stream capture.
