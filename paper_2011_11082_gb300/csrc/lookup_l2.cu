@@ -1,11 +1,12 @@
 // lookup_l2.cu -- fused lookup + rho (Algorithm 5 and corrcoef) for series
-// too long for a target tile to sit in shared memory (T x 128 bytes above
-// the 227 KB a CTA can hold, i.e. T beyond about 3,500 steps with 64-byte
-// rows).
+// too long for a target tile to sit in shared memory (a tile of T rows above
+// the 227 KB a CTA can hold even with 64-byte rows, i.e. T beyond about
+// 3,100 steps).
 //
 // The FP32 tile ([T][32] z-normalised targets, 128-byte time rows) stays in
-// global memory; the host plans target blocks of about 64 MB, so the tiles
-// of a block stay in L2 while every library block sweeps them.  The gathers
+// global memory; the host cuts each E group of tiles into target blocks of
+// about 64 MB, so the tiles of a block stay in L2 while every library block
+// sweeps them.  The gathers
 // are laid out for the L2 -> SM path rather than for shared-memory banks:
 // the eight lanes of a lane group read the eight 16-byte chunks of ONE
 // neighbour row, so every gather instruction of a warp fetches four whole
@@ -168,11 +169,11 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
     }
 }
 
-// One launch per register class for a block of FP32 tiles of mixed E: each
-// CTA runs the variant of its own tile, or returns at once when its tile's
-// K = E + 1 belongs to the other class.  Small K (<= kL2SplitK) keeps two
-// CTAs per SM within 128 registers; larger K gets the registers of one CTA.
-
+// One launch per register class over that class's tiles (mixed E within
+// the class): each CTA runs the variant of its own tile; a tile of the other
+// class (never launched here by launch_lookup_l2) would return at once.
+// Small K = E + 1 (<= kL2SplitK) keeps two CTAs per SM within 128
+// registers; larger K gets the registers of one CTA.
 template <bool kLag, bool kLarge>
 __global__ void __launch_bounds__(kL2Threads, kLarge ? 1 : 2) lookup_l2_kernel(LookupArgs a)
 {
