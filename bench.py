@@ -175,9 +175,19 @@ def cpu_baseline(Y, optE, sample_rows, N, E_max=20):
     per_series_p1 = (t1 - t0) / sample_rows
     per_row_p2 = (t2 - t1) / sample_rows
     est = N * (per_series_p1 + per_row_p2)
+    # the same on one thread (2 series + 2 library rows)
+    one = min(2, sample_rows)
+    t3 = time.perf_counter()
+    orc.optimal_E(Y[:one], E_max, nthreads=1)
+    t4 = time.perf_counter()
+    orc.ccm_rho_rows(Y, optE, rows=rows[:one], nthreads=1)
+    t5 = time.perf_counter()
+    est1 = N * ((t4 - t3) + (t5 - t4)) / one
     return {"value": float(N) * N / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": float(N) * N / est1,
             "sample": f"phase 1 on {sample_rows} series + phase 2 for {sample_rows} library rows x all {N} targets "
-                      f"({t2 - t0:.1f} s of CPU wall time), extrapolated to N={N}"}
+                      f"({t2 - t0:.1f} s of CPU wall time), extrapolated to N={N}; single thread: {one} series + "
+                      f"{one} rows ({t5 - t3:.1f} s)"}
 
 
 def run_reference(args):
