@@ -103,3 +103,30 @@ def test_batched_argument_checks_need_no_gpu(lib):
     assert lib.edm_ccm_rho_batched(narrow, 1, ctypes.byref(p), fake, 1 << 30, None) == 1
     big = (edm_dataset * 1)(edm_dataset(fake, 70000, 500, 500, fake, fake, 70000))  # N beyond 16-bit grid
     assert lib.edm_ccm_rho_batched(big, 1, ctypes.byref(p), fake, 1 << 40, None) == 5
+
+
+def test_long_series_limits_and_workspace_need_no_gpu(lib):
+    """Series beyond the shared-memory tile (about 3,100 steps) are accepted
+    by the cross map (tiles read from L2) up to the kNN staging limit (about
+    46,000 steps); the table area of the workspace shrinks with T."""
+    from paper_2011_11082_gb300 import make_params
+    from paper_2011_11082_gb300._abi import edm_dataset
+
+    p = make_params()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: checks fail first
+    # N = 1,000, T = 40,000: tiles (52 x 40,000 x 128 B) + tables of at
+    # least 16 libraries (all E) -- well under the 14 GB a fixed 256-library
+    # floor would take
+    ws = lib.edm_ccm_workspace_bytes(1000, 40000, ctypes.byref(p))
+    assert 52 * 40000 * 128 < ws < 2 * 1024**3
+    assert lib.edm_ccm_rho(fake, 1000, 40000, 40000, fake, 0, 1000, ctypes.byref(p), fake, 1000, fake, ws - 1,
+                           None) == 3
+    # beyond the kNN staging limit: unsupported, for every entry point
+    for T in (50000, 60000):
+        assert lib.edm_knn_table(fake, 1, T, T, 2, ctypes.byref(p), fake, fake, T - 2, None) == 5
+        assert lib.edm_optimal_E(fake, 1, T, T, ctypes.byref(p), fake, None, None) == 5
+        big = lib.edm_ccm_workspace_bytes(8, T, ctypes.byref(p))
+        assert lib.edm_ccm_rho(fake, 8, T, T, fake, 0, 8, ctypes.byref(p), fake, 8, fake, big, None) == 5
+    # the batched form keeps its tiles in shared memory: about 3,100 steps at most
+    long_set = (edm_dataset * 1)(edm_dataset(0x1000, 64, 5000, 5000, 0x1000, 0x1000, 64))
+    assert lib.edm_ccm_rho_batched(long_set, 1, ctypes.byref(p), fake, 1 << 40, None) == 5
