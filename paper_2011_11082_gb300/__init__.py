@@ -141,6 +141,8 @@ def edm_ccm_rho(Y: torch.Tensor, optE: torch.Tensor, lib_begin: int = 0, lib_cou
     if not (out.is_cuda and out.dtype == torch.float32 and out.dim() == 2 and out.stride(1) == 1
             and out.shape[0] == N and out.shape[1] >= lib_count):
         raise TypeError("out must be a float32 CUDA tensor [N][>=lib_count] with unit inner stride")
+    if lib_count == 0 and 0 <= lib_begin <= N:
+        return out  # an empty library range: nothing to compute (an empty tensor has no data pointer)
     p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision, flags=flags)
     need = int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
     if workspace is None or workspace.numel() < need:
