@@ -64,7 +64,7 @@ def _lookup_sources_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2011_11082_gb300", "csrc")
     # the kernels and the planner (which shapes every launch)
-    for f in ("lookup_chunked.cuh", "lookup_chunked128.cu", "lookup_chunked64.cu", "edm_api.cu"):
+    for f in ("lookup_chunked.cuh", "lookup_multi_impl.cuh", "lookup_chunked128.cu", "lookup_chunked64.cu", "edm_api.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -152,24 +152,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(Y, optE, sample_rows, N, E_max=20):
-    """The FP64 oracle, as it stands, on `sample_rows` library rows x all
-    targets (phase 2) plus phase 1 of as many series; scaled to pairs/s.
-    optE=None: the targets' E are the oracle's phase-1 values of the sampled
-    series, repeated over all N targets."""
+def sample_rows_of(N, sample_rows, seed=7):
+    """Seeded library rows (and series) the oracle samples, spread over all N
+    (so they fall in different library blocks and E groups)."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(N, size=min(N, sample_rows), replace=False)).astype(np.int64)
+
+
+def cpu_baseline(Y, optE, sample_rows, N, E_max=20, keep=None):
+    """The FP64 oracle, as it stands, on `sample_rows` seeded library rows x
+    all targets (phase 2) plus phase 1 of the same series; scaled to
+    pairs/s.  optE=None: the targets' E are the oracle's phase-1 values of
+    the sampled series, repeated over all N targets.  keep (a dict): receives
+    the sampled rows, the oracle's phase-1 optE of those series and its rho
+    rows (library-major), for the parity record."""
     from oracle import oracle as orc
 
     cores = orc.default_threads()
     if sample_rows <= 0:
         sample_rows = 2 * cores
-    rows = np.arange(sample_rows, dtype=np.int64)
+    rows = sample_rows_of(N, sample_rows)
+    sample_rows = rows.size
     t0 = time.perf_counter()
-    oE, _ = orc.optimal_E(Y[:sample_rows], E_max, nthreads=cores)
+    oE, _ = orc.optimal_E(Y[rows], E_max, nthreads=cores)
     t1 = time.perf_counter()
     if optE is None:
         optE = np.resize(oE, N).astype(np.int32)
-    orc.ccm_rho_rows(Y, optE, rows=rows, nthreads=cores)
+    R = orc.ccm_rho_rows(Y, optE, rows=rows, nthreads=cores)
     t2 = time.perf_counter()
+    if keep is not None:
+        keep.update(rows=rows, optE=oE, rho=R)
     # whole-path time for N^2 pairs, extrapolated: phase 1 for N series and
     # phase 2 for N library rows.
     per_series_p1 = (t1 - t0) / sample_rows
@@ -178,16 +190,37 @@ def cpu_baseline(Y, optE, sample_rows, N, E_max=20):
     # the same on one thread (2 series + 2 library rows)
     one = min(2, sample_rows)
     t3 = time.perf_counter()
-    orc.optimal_E(Y[:one], E_max, nthreads=1)
+    orc.optimal_E(Y[rows[:one]], E_max, nthreads=1)
     t4 = time.perf_counter()
     orc.ccm_rho_rows(Y, optE, rows=rows[:one], nthreads=1)
     t5 = time.perf_counter()
     est1 = N * ((t4 - t3) + (t5 - t4)) / one
     return {"value": float(N) * N / est, "unit": UNIT, "cores": cores, "kind": "oracle",
             "single_thread_value": float(N) * N / est1,
-            "sample": f"phase 1 on {sample_rows} series + phase 2 for {sample_rows} library rows x all {N} targets "
+            "sample": f"phase 1 on {sample_rows} seeded series + phase 2 for the same {sample_rows} library rows x "
+                      f"all {N} targets "
                       f"({t2 - t0:.1f} s of CPU wall time), extrapolated to N={N}; single thread: {one} series + "
                       f"{one} rows ({t5 - t3:.1f} s)"}
+
+
+def parity_record(gpu_cols, gpu_optE_rows, keep, tol):
+    """Element-by-element comparison of the GPU's rho on the sampled library
+    rows (gpu_cols: [N targets][rows], target-major columns) and its phase-1
+    optE of the sampled series with the oracle's (keep from cpu_baseline)."""
+    R = keep["rho"]  # [rows][N] library-major
+    G = np.asarray(gpu_cols, dtype=np.float64).T
+    nan_o, nan_g = np.isnan(R), np.isnan(G)
+    both = ~nan_o & ~nan_g
+    err = np.abs(G[both] - R[both])
+    return {"library_rows": int(R.shape[0]), "targets": int(R.shape[1]), "pairs": int(R.size),
+            "max_abs_err": float(err.max()) if err.size else None,
+            "mean_abs_err": float(err.mean()) if err.size else None,
+            "p99_abs_err": float(np.percentile(err, 99)) if err.size else None,
+            "nan_mismatches": int(np.sum(nan_o != nan_g)), "tol": tol,
+            "within_tol": bool(err.size and err.max() < tol and not np.any(nan_o != nan_g)),
+            "optE_series": int(keep["optE"].size),
+            "optE_mismatches": int(np.sum(np.asarray(gpu_optE_rows) != keep["optE"])),
+            "rows": "seeded sample of library rows and series (see cpu_baseline.sample), all targets"}
 
 
 def run_reference(args):
@@ -374,6 +407,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=0, help="library rows the oracle times (0: 2 x cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-target sub-record of an FP32 run")
     ap.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
                     help="dataset-size sweep (one JSON line per size) instead of the benchmark line")
     ap.add_argument("--size", default=None, help="with --sweep: one size NxT instead of the sweep's list")
@@ -416,48 +450,73 @@ def main():
     ws = torch.empty(edm.edm_ccm_workspace_bytes(N, T, precision=prec), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        optE, _ = edm.edm_optimal_E(Yd, E_max=E_max, return_rho=False)
-        edm.edm_ccm_rho(Yd, optE, precision=prec, out=rho, workspace=ws, flags=flags)
-        return optE
+    def timed(prec_k, ws_k, warmup, steps):
+        """W warm-up steps, then K steps between events on the launching
+        stream (barrier + synchronize on both sides), clocks sampled during
+        the timed region; per-kernel times from per-launch events."""
+        def step():
+            optE, _ = edm.edm_optimal_E(Yd, E_max=E_max, return_rho=False)
+            edm.edm_ccm_rho(Yd, optE, precision=prec_k, out=rho, workspace=ws_k, flags=flags)
+            return optE
 
-    for _ in range(args.warmup):
-        optE = step()
-    torch.cuda.synchronize()
+        for _ in range(warmup):
+            optE = step()
+        torch.cuda.synchronize()
+        launches0 = [lib.edm_launch_count(k) for k in range(4)]
+        lib.edm_profile_enable(1)
+        for k in range(4):
+            lib.edm_profile_read(k, None, None, None)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            optE = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop()
+        lib.edm_profile_enable(0)
+        ms = ev0.elapsed_time(ev1) / steps
+        launches = sum(lib.edm_launch_count(k) - launches0[k] for k in range(4))
+        prof = {}
+        for k in range(4):
+            m, n, u = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+            lib.edm_profile_read(k, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
+            prof[_abi.KERNEL_NAMES[k]] = {"ms": m.value / steps, "launches": n.value / steps, "units": u.value / steps}
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, clk, launches, optE
 
-    launches0 = [lib.edm_launch_count(k) for k in range(4)]
-    lib.edm_profile_enable(1)
-    for k in range(4):
-        lib.edm_profile_read(k, None, None, None)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        optE = step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    lib.edm_profile_enable(0)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    launches = sum(lib.edm_launch_count(k) - launches0[k] for k in range(4))
-    prof = {}
-    for k in range(4):
-        m, n, u = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
-        lib.edm_profile_read(k, ctypes.byref(m), ctypes.byref(n), ctypes.byref(u))
-        prof[_abi.KERNEL_NAMES[k]] = {"ms": m.value / args.steps, "launches": n.value / args.steps,
-                                      "units": u.value / args.steps}
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def smem_roofline(prof, optE, s_y, clk):
+        """The bound that holds: the lookup reads every gathered value from
+        shared memory (peak = 128 B/clk/SM x SMs x the SM clock seen)."""
+        hist_now = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:]
+        sm_bytes = _smem_gather_bytes(hist_now, T, 1, s_y, N)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
+        sm_peak = SMEM_BYTES_PER_CLK * n_sm * clk_hz / 1e12
+        lk_ms = prof["lookup_kernel"]["ms"]
+        sm_ach = sm_bytes / (lk_ms / 1e3) / 1e12 if lk_ms > 0 else 0.0
+        return {"bound": "smem", "achieved": sm_ach, "peak": sm_peak, "unit": "TB/s", "frac": sm_ach / sm_peak,
+                "kernel": "lookup_kernel", "bytes_per_step": sm_bytes,
+                "peak_from": f"{SMEM_BYTES_PER_CLK:.0f} B/clk/SM x {n_sm} SMs x {clk_hz / 1e6:.0f} MHz"}
+
+    # parity sample: the library rows (and series) the oracle leg computes
+    cpu_rows = args.cpu_rows if args.cpu_rows > 0 else 2 * (len(os.sched_getaffinity(0)) or 1)
+    par_rows = torch.from_numpy(sample_rows_of(N, cpu_rows)).to(dev)
+
+    ms, prof, clk, launches, optE = timed(prec, ws, args.warmup, args.steps)
     value = world * float(N) * N / (ms / 1e3)
+    gpu_cols = rho.index_select(1, par_rows).cpu().numpy()
+    gpu_optE_rows = optE.index_select(0, par_rows).cpu().numpy()
 
     # roofline of the dominant kernel (lookup): algorithmic bytes / time
     peak, peak_kind = _peaks()
@@ -473,17 +532,25 @@ def main():
                 "peak_kind": peak_kind,
                 "kernel": "lookup_kernel", "bytes_per_pair": bpp,
                 "path_frac": (N * float(N) * bpp / (ms / 1e3) / 1e9) / peak}
-    # the bound that holds: the lookup reads every gathered value from
-    # shared memory (peak = 128 B/clk/SM x SMs x the SM clock seen)
-    hist_now = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:]
-    sm_bytes = _smem_gather_bytes(hist_now, T, 1, s_y, N)
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk_hz = (clk.get("sm_mhz") or 2070.0) * 1e6
-    sm_peak = SMEM_BYTES_PER_CLK * n_sm * clk_hz / 1e12
-    sm_ach = sm_bytes / (lk["ms"] / 1e3) / 1e12 if lk["ms"] > 0 else 0.0
-    roofline_smem = {"bound": "smem", "achieved": sm_ach, "peak": sm_peak, "unit": "TB/s", "frac": sm_ach / sm_peak,
-                     "kernel": "lookup_kernel", "bytes_per_step": sm_bytes,
-                     "peak_from": f"{SMEM_BYTES_PER_CLK:.0f} B/clk/SM x {n_sm} SMs x {clk_hz / 1e6:.0f} MHz"}
+    roofline_smem = smem_roofline(prof, optE, s_y, clk)
+
+    # the FP16-target form on the same workload and steps (FP32 runs stay the
+    # headline): its step time, kernel split and shared-memory roofline
+    fp16 = None
+    f16_cols = None
+    if args.precision == "fp32" and not args.no_fp16:
+        p16 = edm.EDM_PRECISION_FP16_TARGETS
+        ws16 = ws if ws.numel() >= edm.edm_ccm_workspace_bytes(N, T, precision=p16) else \
+            torch.empty(edm.edm_ccm_workspace_bytes(N, T, precision=p16), dtype=torch.uint8, device=dev)
+        ms16, prof16, clk16, launches16, optE16 = timed(p16, ws16, min(args.warmup, 3), args.steps)
+        f16_cols = rho.index_select(1, par_rows).cpu().numpy()
+        fp16 = {"ms_per_step": ms16, "value": world * float(N) * N / (ms16 / 1e3), "unit": UNIT,
+                "steps": args.steps, "warmup": min(args.warmup, 3), "speedup_vs_fp32": ms / ms16,
+                "lookup_speedup_vs_fp32": prof["lookup_kernel"]["ms"] / max(1e-9, prof16["lookup_kernel"]["ms"]),
+                "dtype": "f16-targets/f32-accumulate", "kernels": prof16,
+                "roofline_smem": smem_roofline(prof16, optE16, 2.0, clk16), "clocks": clk16,
+                "gpu_launches": launches16}
+        del ws16
 
     # end to end through the public API with host buffers: edm_ccm_host
     # copies the series in, runs both phases and streams rho back to the host
@@ -524,8 +591,13 @@ def main():
             e2e = {"value": None, "unit": UNIT, "error": repr(ex)[:200]}
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(Y, optE.cpu().numpy(), args.cpu_rows, N, E_max)
+        keep = {}
+        cpu = cpu_baseline(Y, optE.cpu().numpy(), cpu_rows, N, E_max, keep=keep)
+        parity = parity_record(gpu_cols, gpu_optE_rows, keep, 1e-4)
+        if fp16 is not None:
+            fp16["parity"] = parity_record(f16_cols, gpu_optE_rows, keep, 1e-3)
 
     if rank == 0:
         hist = np.bincount(optE.cpu().numpy(), minlength=E_max + 1)[1:].tolist()
@@ -538,7 +610,7 @@ def main():
                        "precision": args.precision, "lookup": args.lookup, "knn": args.knn, "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)",
                        "optE_histogram": hist},
             "roofline": roofline, "roofline_smem": roofline_smem, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "kernels": prof,
+            "gpu_launches": launches, "kernels": prof, "parity": parity, "fp16": fp16,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -70,4 +70,34 @@ __device__ __forceinline__ unsigned long long dkey(float d, int s)
 // per accumulation), widened to E+3 for margin.
 __device__ __forceinline__ float d2_err(float d, int E) { return d * (float)(E + 3) * 5.9604645e-8f; }
 
+// Pearson rho of one (library, target) pair (Algorithm 1/2, corrcoef) from
+// FP32 moment sums over its n query rows: sd = sum(p - K), sdd =
+// sum((p - K)^2), sdo = sum((p - K) o) for any shift K of the predictions p
+// (it cancels), so_ = sum(o), dvo = n sum(o^2) - so_^2.  The centred
+// numerator n sdo - sd so_ and variance n sdd - sd^2 are single fused
+// operations (the callers guarantee a well-conditioned variance: mean^2 at
+// most 7x the variance, else shifted sums); the variance product and its
+// normalisation of the numerator are FP64.  A side of zero variance gives
+// NaN.
+__device__ __forceinline__ float rho_final(float sd, float sdd, float sdo, float so_, float dvo, int nrows)
+{
+    const float n = (float)nrows;
+    const float den_p = fmaf(n, sdd, -sd * sd);
+    if (!(den_p > 0.f) || !(dvo > 0.f))
+        return CUDART_NAN_F;
+    const float num = fmaf(n, sdo, -sd * so_);
+    return (float)((double)num * rsqrt((double)den_p * (double)dvo));
+}
+
+// Conditioning test of unshifted prediction sums (sp = sum p, spp = sum p^2):
+// true when the mean is large against the spread (n spp / (n spp - sp^2)
+// above 8), where n spp - sp^2 from FP32 sums loses digits; the caller then
+// sums again with the predictions shifted by one row's prediction.
+__device__ __forceinline__ bool moments_ill_conditioned(float sp, float spp, int nrows)
+{
+    const float n = (float)nrows;
+    const float den_p = fmaf(n, spp, -sp * sp);
+    return !(8.f * den_p > n * spp);
+}
+
 }  // namespace edm

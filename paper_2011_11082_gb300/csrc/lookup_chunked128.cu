@@ -1,72 +1,15 @@
 // lookup_chunked128.cu -- the chunked lookup for 128-byte tile rows
-// (32 FP32 / 64 FP16 targets per row; series up to about 1,500 steps).
-#include "lookup_chunked.cuh"
-
+// (32 FP32 / 64 FP16 targets per row; series up to about 1,500 steps), the
+// FP16 target staging and the dispatch over row widths and forms.
 #define EDM_RB 128
+#define EDM_LAG false
 #define EDM_MULTI_NAME lookup_multi128_kernel
 #define EDM_MULTI_LAUNCH launch_lookup_multi128
+#include "lookup_multi_impl.cuh"
 
 namespace edm {
 
 size_t chunked_smem_bytes(int T, int RB) { return 128 + (size_t)T * RB + (size_t)kCkWarps * 32 * kCkRed * 4; }
-
-// One launch for a block of tiles of mixed E (and FP16/FP32 tiles): each
-// CTA runs the variant of its own tile, so a CTA only ever executes one
-// specialisation's code.
-template <bool kLag>
-__global__ void __launch_bounds__(kCkThreads, 1) EDM_MULTI_NAME(LookupArgs a)
-{
-    const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
-    const bool f16 = (m.flags & kTileF16) != 0;
-#define EDM_MK(KK)                                                                                                     \
-    case KK:                                                                                                           \
-        if (f16 && KK <= kF16MaxK)                                                                                     \
-            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true, EDM_RB, kLag>(a);                                                     \
-        else                                                                                                           \
-            lookup_chunk_body<KK, false, EDM_RB, kLag>(a);                                                                           \
-        break;
-    switch (m.E + 1) {
-        EDM_MK(2)
-        EDM_MK(3)
-        EDM_MK(4)
-        EDM_MK(5)
-        EDM_MK(6)
-        EDM_MK(7)
-        EDM_MK(8)
-        EDM_MK(9)
-        EDM_MK(10)
-        EDM_MK(11)
-        EDM_MK(12)
-        EDM_MK(13)
-        EDM_MK(14)
-        EDM_MK(15)
-        EDM_MK(16)
-        EDM_MK(17)
-        EDM_MK(18)
-        EDM_MK(19)
-        EDM_MK(20)
-        EDM_MK(21)
-    default: break;
-    }
-#undef EDM_MK
-}
-
-cudaError_t EDM_MULTI_LAUNCH(const LookupArgs &a, cudaStream_t st)
-{
-    if (a.n_tiles <= 0 || a.n_lib <= 0)
-        return cudaSuccess;
-    size_t smem = chunked_smem_bytes(a.T, EDM_RB);
-    // the time-delay form is a separate instantiation, so the plain cross
-    // map keeps its register allocation
-    const bool lag = a.s_lo != 0 || a.lag != a.Tp;
-    void (*kern)(LookupArgs) = lag ? EDM_MULTI_NAME<true> : EDM_MULTI_NAME<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
-    kern<<<grid, kCkThreads, smem, st>>>(a);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // FP16 staging: 64 targets per tile, z-normalised in FP64 then rounded to
@@ -144,11 +87,18 @@ cudaError_t launch_prep_targets_f16(const float *Y, int64_t ldY, int T, int tau,
     return cudaGetLastError();
 }
 
+cudaError_t launch_lookup_multi128_lag(const LookupArgs &a, cudaStream_t st);
 cudaError_t launch_lookup_multi64(const LookupArgs &a, cudaStream_t st);
+cudaError_t launch_lookup_multi64_lag(const LookupArgs &a, cudaStream_t st);
 
+// The time-delay form is a separate instantiation, so the plain cross map
+// keeps its register allocation.
 cudaError_t launch_lookup_multi(const LookupArgs &a, int RB, cudaStream_t st)
 {
-    return RB == 128 ? launch_lookup_multi128(a, st) : launch_lookup_multi64(a, st);
+    const bool lag = a.s_lo != 0 || a.lag != a.Tp;
+    if (RB == 128)
+        return lag ? launch_lookup_multi128_lag(a, st) : launch_lookup_multi128(a, st);
+    return lag ? launch_lookup_multi64_lag(a, st) : launch_lookup_multi64(a, st);
 }
 
 int chunked_row_bytes(int T)

@@ -9,7 +9,11 @@
 // r the 32 lanes read 32 different columns, so every gather hits 32
 // distinct banks whatever the neighbour rows are.  Moment sums per
 // (lane, r) are folded into per-target sums through a small shared
-// transpose at the end of the library.
+// transpose at the end of the library.  Every prediction enters the sums
+// shifted by the prediction of the last table row of its (library, target)
+// pair (kept per warp in shared memory, formed by the same operations), so
+// nearly constant predictions keep their variance and equal ones give zero
+// variance; rho is formed in FP64.
 #include "edm_internal.cuh"
 #include <cuda_fp16.h>
 
@@ -23,7 +27,47 @@ constexpr int kRedStride = 33;
 
 // 128 spare bytes let the tile start on a 128-byte boundary of the shared
 // window, which the XOR addressing of the gathers relies on.
-size_t lookup_smem_bytes(int T) { return 128 + (size_t)T * 32 * sizeof(float) + (size_t)kLkWarps * 32 * kRedStride * 4; }
+size_t lookup_smem_bytes(int T)
+{
+    return 128 + (size_t)T * 32 * sizeof(float) + (size_t)kLkWarps * 32 * kRedStride * 4 + (size_t)kLkWarps * 32 * 4;
+}
+
+// Per-target shift of one library: the prediction of table row R for
+// target column `lane` (same operation order as every other row), stored
+// at sh[lane].
+__device__ __forceinline__ void lookup_row_shift(const float *Wt, const uint16_t *It, size_t tq_pad, int k, int R,
+                                                 uint32_t base, float *sh)
+{
+    const int lane = lane_id();
+    float p = 0.f;
+    for (int n = 0; n < k; ++n) {
+        const float w = __ldg(Wt + (size_t)n * tq_pad + R);
+        const uint32_t i = __ldg(It + (size_t)n * tq_pad + R);
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(base + i * 128u + (uint32_t)lane * 4u));
+        p = fmaf(w, v, p);
+    }
+    __syncwarp();
+    sh[lane] = p;
+    __syncwarp();
+}
+
+// Sum for target `lane` of the per-(lane, slot) sums S[r] of slot r =
+// target lane ^ r in every lane (through red; four chains, then pairwise).
+__device__ __forceinline__ float fold_xor(float *red, const float *S)
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        red[r * kRedStride + lane] = S[r];
+    __syncwarp();
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int l2 = 0; l2 < 32; ++l2)
+        s[l2 & 3] += red[(lane ^ l2) * kRedStride + l2];
+    __syncwarp();
+    return (s[0] + s[1]) + (s[2] + s[3]);
+}
 
 __device__ __forceinline__ float lds_f32(uint32_t addr)
 {
@@ -155,6 +199,7 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_generic_kernel(LookupArg
     unsigned char *smem = smem_raw + pad;
     float *tile_s = reinterpret_cast<float *>(smem);
     float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * 32 * sizeof(float));
+    float *sh_all = red_all + kLkWarps * 32 * kRedStride;
     const uint32_t base = raw + pad;
 
     const int tile = a.tile_begin + blockIdx.x;
@@ -175,6 +220,8 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_generic_kernel(LookupArg
 
     const int lane = lane_id(), warp = warp_id();
     float *red = red_all + warp * 32 * kRedStride;
+    float *sh = sh_all + warp * 32;
+    const uint32_t sh_base = (uint32_t)__cvta_generic_to_shared(sh);
     const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
     const int lib_lo = blockIdx.y * per;
     const int lib_hi = min(a.n_lib, lib_lo + per);
@@ -184,6 +231,7 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_generic_kernel(LookupArg
         const uint8_t *lb = a.tables + (size_t)lib * a.lay.lib_stride;
         const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
         const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        lookup_row_shift(Wt, It, (size_t)a.lay.Tq_pad, k, Tq - 1, base, sh);
         float Sp[32], Spp[32], Spo[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
@@ -215,35 +263,18 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_generic_kernel(LookupArg
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
                 float o = lds_f32(Ao ^ (uint32_t)(r * 4));
-                Sp[r] += p[r];
-                Spp[r] = fmaf(p[r], p[r], Spp[r]);
-                Spo[r] = fmaf(p[r], o, Spo[r]);
+                const float pr = valid ? p[r] - lds_f32(sh_base ^ (uint32_t)(r * 4) ^ lane4) : 0.f;
+                Sp[r] += pr;
+                Spp[r] = fmaf(pr, pr, Spp[r]);
+                Spo[r] = fmaf(pr, o, Spo[r]);
             }
         }
         // per-target sums: target c collects slot c^l of every lane l
-        float tot[3];
-#pragma unroll
-        for (int mm = 0; mm < 3; ++mm) {
-            const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
-#pragma unroll
-            for (int r = 0; r < 32; ++r)
-                red[r * kRedStride + lane] = S[r];
-            __syncwarp();
-            float s = 0.f;
-#pragma unroll
-            for (int l2 = 0; l2 < 32; ++l2)
-                s += red[(lane ^ l2) * kRedStride + l2];
-            tot[mm] = s;
-            __syncwarp();
-        }
+        const float t0 = fold_xor(red, Sp), t1 = fold_xor(red, Spp), t2 = fold_xor(red, Spo);
         if (lane < m.count) {
             const int64_t j = a.pi[m.first + lane];
             const float2 om = a.omom[m.first + lane];
-            const float n = (float)Tq;
-            const float num = n * tot[2] - tot[0] * om.x;
-            const float den_p = n * tot[1] - tot[0] * tot[0];
-            const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;
-            a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho;
+            a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho_final(t0, t1, t2, om.x, om.y, Tq);
         }
     }
 }
@@ -263,6 +294,7 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_k_kernel(LookupArgs a)
     unsigned char *smem = smem_raw + pad;
     float *tile_s = reinterpret_cast<float *>(smem);
     float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * 32 * sizeof(float));
+    float *sh_all = red_all + kLkWarps * 32 * kRedStride;
     const uint32_t base = raw + pad;
 
     const int tile = a.tile_begin + blockIdx.x;
@@ -283,6 +315,8 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_k_kernel(LookupArgs a)
 
     const int lane = lane_id(), warp = warp_id();
     float *red = red_all + warp * 32 * kRedStride;
+    float *sh = sh_all + warp * 32;
+    const uint32_t sh_base = (uint32_t)__cvta_generic_to_shared(sh);
     const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
     const int lib_lo = blockIdx.y * per;
     const int lib_hi = min(a.n_lib, lib_lo + per);
@@ -293,6 +327,7 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_k_kernel(LookupArgs a)
         const uint8_t *lb = a.tables + (size_t)lib * a.lay.lib_stride;
         const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
         const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        lookup_row_shift(Wt, It, tq_pad, K, Tq - 1, base, sh);
         float Sp[32], Spp[32], Spo[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
@@ -339,34 +374,17 @@ __global__ void __launch_bounds__(kLkThreads, 1) lookup_k_kernel(LookupArgs a)
                 for (int n = 0; n < K; ++n)
                     p = fmaf(wn[n], lds_f32(An[n] ^ x), p);
                 const float o = lds_f32(Ao ^ x);
+                p = valid ? p - lds_f32(sh_base ^ x ^ lane4) : 0.f;
                 Sp[r] += p;
                 Spp[r] = fmaf(p, p, Spp[r]);
                 Spo[r] = fmaf(p, o, Spo[r]);
             }
         }
-        float tot[3];
-#pragma unroll
-        for (int mm = 0; mm < 3; ++mm) {
-            const float *S = mm == 0 ? Sp : (mm == 1 ? Spp : Spo);
-#pragma unroll
-            for (int r = 0; r < 32; ++r)
-                red[r * kRedStride + lane] = S[r];
-            __syncwarp();
-            float sacc = 0.f;
-#pragma unroll
-            for (int l2 = 0; l2 < 32; ++l2)
-                sacc += red[(lane ^ l2) * kRedStride + l2];
-            tot[mm] = sacc;
-            __syncwarp();
-        }
+        const float t0 = fold_xor(red, Sp), t1 = fold_xor(red, Spp), t2 = fold_xor(red, Spo);
         if (lane < m.count) {
             const int64_t j = a.pi[m.first + lane];
             const float2 om = a.omom[m.first + lane];
-            const float n = (float)Tq;
-            const float num = n * tot[2] - tot[0] * om.x;
-            const float den_p = n * tot[1] - tot[0] * tot[0];
-            const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;
-            a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho;
+            a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho_final(t0, t1, t2, om.x, om.y, Tq);
         }
     }
 }

@@ -16,7 +16,10 @@
 // table entries (weight, neighbour time) of one query row per 32-row block,
 // one block ahead, and the groups fetch the entries of their current row by
 // warp shuffles.  Moment sums are two-level (per 32-row block, then over
-// blocks) so the FP32 error stays small at T in the tens of thousands.
+// blocks) so the FP32 error stays small at T in the tens of thousands, of
+// predictions shifted by the prediction of the last table row (so nearly
+// constant predictions keep their variance and equal ones give zero
+// variance); rho is formed in FP64.
 #include <algorithm>
 
 #include "edm_internal.cuh"
@@ -77,6 +80,24 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
             Spp[i] = 0.f;
             Spo[i] = 0.f;
         }
+        // shift: the prediction of the last table row (same operations as
+        // every other row), subtracted from every prediction
+        float4 shn;
+        {
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int R = Tq - 1;
+#pragma unroll
+            for (int n = 0; n < K; ++n) {
+                const float w = __ldg(Wt + n * tq_pad + R);
+                const int off = ((int)__ldg(It + n * tq_pad + R) + dshift) * 8;
+                const float4 v = ldg_v4(tsub + off);
+                p.x = fmaf(w, v.x, p.x);
+                p.y = fmaf(w, v.y, p.y);
+                p.z = fmaf(w, v.z, p.z);
+                p.w = fmaf(w, v.w, p.w);
+            }
+            shn = make_float4(-p.x, -p.y, -p.z, -p.w);
+        }
         // table entries of row r_lo + 32 b + lane (row offsets in float4 units)
         float wq[K];
         int iq[K];
@@ -125,7 +146,8 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
                 }
                 if (row < Tq) {
                     const float4 o = ldg_v4(tsub + (size_t)(L + row + lag) * 8);
-                    const float pp[4] = {p.x, p.y, p.z, p.w}, oo[4] = {o.x, o.y, o.z, o.w};
+                    const float pp[4] = {p.x + shn.x, p.y + shn.y, p.z + shn.z, p.w + shn.w};
+                    const float oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         bp[i] += pp[i];
@@ -158,11 +180,7 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
                 if (t < m.count) {
                     const int64_t j = a.pi[m.first + t];
                     const float2 om = a.omom[m.first + t];
-                    const float n = (float)nrows;
-                    const float num = n * Spo[i] - Sp[i] * om.x;
-                    const float den_p = n * Spp[i] - Sp[i] * Sp[i];
-                    const float rho = (den_p > 0.f && om.y > 0.f) ? num / sqrtf(den_p * om.y) : CUDART_NAN_F;
-                    a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho;
+                    a.rho[j * a.ld_rho + a.rho_col0 + lib] = rho_final(Sp[i], Spp[i], Spo[i], om.x, om.y, nrows);
                 }
             }
         }
