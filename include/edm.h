@@ -262,24 +262,27 @@ size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *
 
 /*
  * Allocation-free variant of edm_ccm_rho, for callers that cannot allocate
- * device memory while they run (code inside a stream capture, where
- * cudaMalloc is not allowed; real-time loops that must not touch an
- * allocator; hosts that hand this library a stream but no memory pool).
+ * device memory while they run: real-time loops that must not touch an
+ * allocator, and hosts that hand this library a stream but no memory pool
+ * (plugins and embedded runtimes that own all device memory themselves).
  * The paper has no counterpart: this is a deployment form of the same
- * cross map.  Inputs, outputs and results are those of edm_ccm_rho; the
- * scratch lives in one statically allocated 64 MiB device array instead of
- * a caller workspace, and the plan is built on the device, so the call
- * makes no cudaMalloc/cudaFree, no allocating library call and no host heap
- * allocation.
+ * cross map.  Inputs, outputs and results are those of edm_ccm_rho (with
+ * params->flags limited to EDM_FLAG_KNN_WARP; any other flag returns
+ * EDM_ERR_UNSUPPORTED); the scratch lives in one statically allocated
+ * 64 MiB device array instead of a caller workspace, and the plan is built
+ * on the device, so the call makes no cudaMalloc/cudaFree, no allocating
+ * library call and no host heap allocation.
  *   - Problems whose scratch exceeds the array (target tiles of about
  *     N*T*4 bytes plus the kNN tables of at least one library) return
  *     EDM_ERR_WORKSPACE before touching the device; e.g. N = 2,048 and
  *     T = 1,500 fit, N = 16,384 and T = 1,500 do not.  Series longer than
  *     a shared-memory target tile allows (about 3,100 steps) return
- *     EDM_ERR_UNSUPPORTED.
+ *     EDM_ERR_UNSUPPORTED.  An optE value outside 1..EDM_MAX_E returns
+ *     EDM_ERR_INVALID.
  *   - The first call on each device resolves the array's device address
- *     (cudaGetSymbolAddress, that device current); make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress, that device current) and keeps it; make that
+ *     first call before any stream capture.  A device reset after it is not
+ *     supported.
  *   - Every GPU that loads the library holds the array until the process
  *     exits.  All calls share it and it keeps the previous call's contents;
  *     calls whose GPU work overlaps (other streams, other host threads)
@@ -305,6 +308,16 @@ int64_t edm_last_bad_series(void);
  * clears them after reading).  Synchronises the device.
  */
 int edm_knn_counters(int64_t *reranks, int64_t *exhaustive, int reset);
+
+/*
+ * Bounded device waits that gave up on the current device since load (or
+ * the last reset != 0): the kNN and lookup kernels stage their series and
+ * target tiles in shared memory with bulk copies completed on an mbarrier,
+ * and poll it a bounded number of times.  A wait that gives up makes its
+ * CTA skip its work (its outputs are left unwritten) and counts here, so a
+ * healthy run reads 0.  Synchronises the device.
+ */
+int edm_wait_timeouts(int64_t *count, int reset);
 
 /* Human-readable text for a status code (includes the CUDA error if any). */
 const char *edm_status_string(int status);

@@ -37,6 +37,7 @@ __all__ = [
     "edm_ccm_backward_workspace_bytes",
     "edm_ccm_rho_batched",
     "edm_knn_counters",
+    "edm_wait_timeouts",
     "CCMBatch",
     "ccm",
     "ccm_rho_autograd",
@@ -112,6 +113,15 @@ def edm_knn_counters(reset: bool = True) -> tuple[int, int]:
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _abi.check(lib.edm_knn_counters(ctypes.byref(a), ctypes.byref(b), 1 if reset else 0), "edm_knn_counters")
     return int(a.value), int(b.value)
+
+
+def edm_wait_timeouts(reset: bool = True) -> int:
+    """Bounded bulk-copy waits of the kNN and lookup kernels that gave up
+    since the last reset (0 in a healthy run; synchronises)."""
+    lib = _abi.load()
+    a = ctypes.c_int64()
+    _abi.check(lib.edm_wait_timeouts(ctypes.byref(a), 1 if reset else 0), "edm_wait_timeouts")
+    return int(a.value)
 
 
 def edm_ccm_workspace_bytes(N: int, T: int, tau: int = 1, Tp: int = 1, exclusion_radius: int = 0,

@@ -73,6 +73,7 @@ SIGNATURES = {
     "edm_ccm_rho_batched_reset": (ctypes.c_int, []),
     "edm_last_bad_series": (ctypes.c_int64, []),
     "edm_knn_counters": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+    "edm_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "edm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "edm_last_cuda_error": (ctypes.c_int, []),
     "edm_version": (ctypes.c_int, []),

@@ -6,12 +6,14 @@
 // The scratch array below is a file-scope __device__ object: every GPU that
 // loads this library holds it until the process exits.  Host code never
 // uses its name as an address; the first call on each device resolves the
-// device address with cudaGetSymbolAddress (that device current) and keeps
-// it for later calls.  All calls share the array and see the previous
+// device address with cudaGetSymbolAddress (that device current, under a
+// lock) and keeps it for later calls, so a device reset after that first
+// call is not supported.  All calls share the array and see the previous
 // call's contents; the kernels write everything they read except the E
 // counters of the plan, which the plan kernel clears itself.  Calls whose
 // GPU work overlaps (different streams, or host threads) race on the array.
 #include <cstdio>
+#include <mutex>
 
 #include "launchers.h"
 
@@ -25,6 +27,7 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
 
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -147,6 +150,11 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
         return EDM_ERR_INVALID;
     if (lib_begin < 0 || lib_count < 0 || lib_begin + lib_count > N || ld_rho < lib_count)
         return EDM_ERR_INVALID;
+    // this call always builds tables with the warp kernel (EDM_FLAG_KNN_WARP
+    // changes nothing); the non-finite scan and the scalar-gather lookup are
+    // not offered here
+    if (params->flags & ~EDM_FLAG_KNN_WARP)
+        return EDM_ERR_UNSUPPORTED;
     if (T > EDM_MAX_T || N > 0x7fffffffLL || T > knn_max_T() || chunked_row_bytes((int)T) == 0)
         return EDM_ERR_UNSUPPORTED;
     const bool f16 = params->precision == EDM_PRECISION_FP16_TARGETS;
@@ -163,14 +171,19 @@ extern "C" int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return EDM_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_ccm_scratch);
-        if (e != cudaSuccess || !ptr)
-            return EDM_ERR_CUDA;
-        g_scratch_ptr[dev] = ptr;
+    void *ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_ccm_scratch);
+            if (e != cudaSuccess || !g_scratch_ptr[dev]) {
+                g_scratch_ptr[dev] = nullptr;
+                return EDM_ERR_CUDA;
+            }
+        }
+        ptr = g_scratch_ptr[dev];
     }
-    unsigned char *ws = (unsigned char *)g_scratch_ptr[dev];
+    unsigned char *ws = (unsigned char *)ptr;
     cudaStream_t st = (cudaStream_t)stream;
     int32_t *counts_d = (int32_t *)(ws + L.counts);
     int32_t *pi_d = (int32_t *)(ws + L.pi);

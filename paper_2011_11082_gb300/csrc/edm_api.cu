@@ -299,6 +299,25 @@ int edm_knn_counters(int64_t *reranks, int64_t *exhaustive, int reset)
     return EDM_OK;
 }
 
+int edm_wait_timeouts(int64_t *count, int reset)
+{
+    cudaError_t (*readers[])(unsigned long long *, bool) = {
+        edm::knn_wait_timeouts, edm::knn_thread_wait_timeouts, edm::lookup_multi128_wait_timeouts,
+        edm::lookup_multi128_lag_wait_timeouts, edm::lookup_multi64_wait_timeouts,
+        edm::lookup_multi64_lag_wait_timeouts};
+    unsigned long long tot = 0ull;
+    for (auto rd : readers) {
+        unsigned long long c = 0ull;
+        cudaError_t e = rd(&c, reset != 0);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        tot += c;
+    }
+    if (count)
+        *count = (int64_t)tot;
+    return EDM_OK;
+}
+
 const char *edm_status_string(int status)
 {
     switch (status) {

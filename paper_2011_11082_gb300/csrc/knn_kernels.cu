@@ -2,6 +2,7 @@
 // tables on sm_103a.  Both stage one series in shared memory and run the
 // warp-per-query kNN of knn_core.cuh (Algorithm 3's all-to-all distances
 // computed on the fly, no materialised embedding).
+#include "bulk_copy.cuh"
 #include "knn_core.cuh"
 #include "launchers.h"
 
@@ -53,15 +54,7 @@ __device__ __forceinline__ float *warp_d2s(KnnWarpScratch *scratch, int J)
     return reinterpret_cast<float *>(scratch + kKnnWarps) + (size_t)warp_id() * 32 * J;
 }
 
-// Stage series `src` (T floats) into xs[-front .. T + tail) with +inf
-// padding: a lag that falls outside the series makes the distance +inf.
-__device__ __forceinline__ void stage_series(float *xs_base, const float *__restrict__ src, int T, int front, int total)
-{
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        int t = i - front;
-        xs_base[i] = (t >= 0 && t < T) ? src[t] : CUDART_INF_F;
-    }
-}
+EDM_WAIT_TIMEOUT_READER(knn_wait_timeouts)
 
 // ---------------------------------------------------------------------------
 // Phase 1: simplex projection of every series over E = 1..E_max.
@@ -117,8 +110,10 @@ __global__ void __launch_bounds__(kKnnThreads, 2) simplex_kernel(const float *__
     __shared__ double rho_sh[EDM_MAX_E];
 
     const int64_t i = blockIdx.x;
-    stage_series(reinterpret_cast<float *>(smem), Y + i * ldY, T, front, total);
-    __syncthreads();
+    // the series in shared memory with +inf padding (a lag that falls
+    // outside the series makes the distance +inf)
+    if (!stage_series_bulk(reinterpret_cast<float *>(smem), Y + i * ldY, T, front, total))
+        return;
 
     // shift for the moments: the series mean (Pearson is shift invariant)
     if (threadIdx.x < 32) {
@@ -260,15 +255,15 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
     KnnWarpScratch *scratch = reinterpret_cast<KnnWarpScratch *>(smem + (size_t)total * sizeof(float));
 
     const int lib = blockIdx.y;
-    stage_series(reinterpret_cast<float *>(smem), Y + (lib0 + lib) * ldY, T, front, total);
-    __syncthreads();
-
-    const int warp = warp_id();
-    KnnWarpScratch &sc = scratch[warp];
     if (sel_dev)
         sel &= *sel_dev;  // E set planned on the device
     if (!sel)
         return;
+    if (!stage_series_bulk(reinterpret_cast<float *>(smem), Y + (lib0 + lib) * ldY, T, front, total))
+        return;
+
+    const int warp = warp_id();
+    KnnWarpScratch &sc = scratch[warp];
     const int E_hi = 32 - __clz(sel);  // highest selected E
     int E_lo = __ffs(sel);             // lowest selected E
     // queries and candidates start at s_lo as well (0 for the plain cross map)

@@ -19,10 +19,13 @@
 // kernel, whose distance sweep serves every E at once).
 #include <cuda_fp16.h>
 
+#include "bulk_copy.cuh"
 #include "edm_internal.cuh"
 #include "launchers.h"
 
 namespace edm {
+
+EDM_WAIT_TIMEOUT_READER(knn_thread_wait_timeouts)
 
 namespace {
 
@@ -64,11 +67,8 @@ __global__ void __launch_bounds__(kTqThreads, (E <= 8 ? 4 : 2))
     const int lib = blockIdx.y;
     const float *src = Y + (lib0 + lib) * ldY;
     const int total = (int)tq_smem_floats(T, E);
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int t = i - F;
-        xs_base[i] = (t >= 0 && t < T) ? src[t] : CUDART_INF_F;
-    }
-    __syncthreads();
+    if (!stage_series_bulk(xs_base, src, T, F, total))
+        return;
 
     const int Tq = T - Tp - (E - 1);
     const int r = blockIdx.x * kTqThreads + threadIdx.x;

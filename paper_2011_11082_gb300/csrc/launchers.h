@@ -58,6 +58,14 @@ cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, in
 // current device (synchronises); reset clears them.
 cudaError_t knn_counters(unsigned long long out[2], bool reset);
 
+// Bounded bulk-copy waits that gave up, per translation unit (bulk_copy.cuh).
+cudaError_t knn_wait_timeouts(unsigned long long *count, bool reset);
+cudaError_t knn_thread_wait_timeouts(unsigned long long *count, bool reset);
+cudaError_t lookup_multi128_wait_timeouts(unsigned long long *count, bool reset);
+cudaError_t lookup_multi128_lag_wait_timeouts(unsigned long long *count, bool reset);
+cudaError_t lookup_multi64_wait_timeouts(unsigned long long *count, bool reset);
+cudaError_t lookup_multi64_lag_wait_timeouts(unsigned long long *count, bool reset);
+
 // Public table format: idx int32 [n_lib][Tq][E+1] (unshifted), w float [n_lib][Tq][E+1].
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
                               int32_t *idx, float *w, cudaStream_t st, bool force_warp = false);

@@ -16,6 +16,7 @@
 // FMA per gathered value, as in the FP32 form, at half the shared bytes.
 #pragma once
 
+#include "bulk_copy.cuh"
 #include "edm_internal.cuh"
 #include "launchers.h"
 
@@ -444,14 +445,22 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
     cx.tq_pad = (size_t)a.lay.Tq_pad;
 
     {
-        const float4 *src = reinterpret_cast<const float4 *>(
-            reinterpret_cast<const unsigned char *>(a.tiles) + (size_t)tile * a.T * RB);
-        float4 *dst = reinterpret_cast<float4 *>(smem);
-        const int n4 = a.T * (RB / 16);
-        for (int i = threadIdx.x; i < n4; i += blockDim.x)
-            dst[i] = __ldg(src + i);
+        // the tile (T rows of RB bytes, 16-byte aligned, a multiple of 16
+        // bytes) by one bulk copy into shared memory; the barrier word sits
+        // behind the per-warp fold buffers
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(a.tiles) + (size_t)tile * a.T * RB;
+        const uint32_t bytes = (uint32_t)a.T * (uint32_t)RB;
+        const uint32_t bar = cx.base + bytes + (uint32_t)(kCkWarps * 32 * kCkRed * 4);
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, bytes);
+            bulk_g2s(cx.base, src, bytes, bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(bar, 0);
+        if (!__syncthreads_and(ok))
+            return;
     }
-    __syncthreads();
 
     const int lane = lane_id(), warp = warp_id();
     float *red = red_all + warp * 32 * kCkRed;

@@ -5,11 +5,13 @@
 #define EDM_LAG false
 #define EDM_MULTI_NAME lookup_multi128_kernel
 #define EDM_MULTI_LAUNCH launch_lookup_multi128
+#define EDM_MULTI_TIMEOUTS lookup_multi128_wait_timeouts
 #include "lookup_multi_impl.cuh"
 
 namespace edm {
 
-size_t chunked_smem_bytes(int T, int RB) { return 128 + (size_t)T * RB + (size_t)kCkWarps * 32 * kCkRed * 4; }
+// alignment pad, the tile, the per-warp fold buffers, the tile's barrier word
+size_t chunked_smem_bytes(int T, int RB) { return 128 + (size_t)T * RB + (size_t)kCkWarps * 32 * kCkRed * 4 + 16; }
 
 // ---------------------------------------------------------------------------
 // FP16 staging: 64 targets per tile, z-normalised in FP64 then rounded to

@@ -3,4 +3,5 @@
 #define EDM_LAG false
 #define EDM_MULTI_NAME lookup_multi64_kernel
 #define EDM_MULTI_LAUNCH launch_lookup_multi64
+#define EDM_MULTI_TIMEOUTS lookup_multi64_wait_timeouts
 #include "lookup_multi_impl.cuh"

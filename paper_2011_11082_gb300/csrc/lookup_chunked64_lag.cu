@@ -3,4 +3,5 @@
 #define EDM_LAG true
 #define EDM_MULTI_NAME lookup_multi64_lag_kernel
 #define EDM_MULTI_LAUNCH launch_lookup_multi64_lag
+#define EDM_MULTI_TIMEOUTS lookup_multi64_lag_wait_timeouts
 #include "lookup_multi_impl.cuh"

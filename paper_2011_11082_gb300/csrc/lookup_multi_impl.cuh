@@ -1,8 +1,9 @@
 // lookup_multi_impl.cuh -- one instantiation of the multi-variant chunked
 // lookup kernel and its launcher.  The including file defines EDM_RB (tile
-// row bytes, 128 or 64), EDM_LAG (time-delay form), EDM_MULTI_NAME (kernel)
-// and EDM_MULTI_LAUNCH (launcher); each combination is its own translation
-// unit so the variants compile in parallel.
+// row bytes, 128 or 64), EDM_LAG (time-delay form), EDM_MULTI_NAME (kernel),
+// EDM_MULTI_LAUNCH (launcher) and EDM_MULTI_TIMEOUTS (reader of the unit's
+// bounded-wait counter); each combination is its own translation unit so the
+// variants compile in parallel.
 #include "lookup_chunked.cuh"
 
 namespace edm {
@@ -46,6 +47,8 @@ __global__ void __launch_bounds__(kCkThreads, 1) EDM_MULTI_NAME(LookupArgs a)
     }
 #undef EDM_MK
 }
+
+EDM_WAIT_TIMEOUT_READER(EDM_MULTI_TIMEOUTS)
 
 cudaError_t EDM_MULTI_LAUNCH(const LookupArgs &a, cudaStream_t st)
 {

@@ -280,3 +280,21 @@ def test_knn_fp64_fallback_counts(edm):
     torch.cuda.synchronize()
     rr2, ex2 = edm.edm_knn_counters(reset=True)
     assert rr2 + ex2 > 0
+
+
+def test_bulk_copies_complete_and_unaligned_rows(edm):
+    """Series rows and target tiles reach shared memory by bulk copies on an
+    mbarrier (16-byte aligned rows) or plain loads (other rows): both give
+    the oracle's results, and no bounded wait gives up."""
+    edm.edm_wait_timeouts(reset=True)
+    # T = 301 with a row pitch of 301 floats: most rows start off a 16-byte
+    # boundary (plain staging); a padded pitch of 304 aligns every row
+    Y = synth.coupled_logistic(40, 301, 0.05, 0.05, seed_data=91, seed_noise=92)
+    E = np.random.default_rng(93).integers(1, 7, size=40).astype(np.int32)
+    R = orc.ccm_rho_rows(Y, E, rows=np.arange(6))
+    for pitch in (301, 304):
+        buf = torch.zeros((40, pitch), dtype=torch.float32, device="cuda")
+        buf[:, :301] = _dev(Y)
+        got = edm.edm_ccm_rho(buf[:, :301], torch.from_numpy(E).cuda()).cpu().numpy()[:, :6].T
+        assert np.abs(got - R).max() < RHO_TOL, pitch
+    assert edm.edm_wait_timeouts(reset=True) == 0
