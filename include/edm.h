@@ -124,8 +124,15 @@ int edm_knn_table(const float *Y, int64_t n_lib, int64_t T, int64_t ldY, int32_t
  *          for every target j in 0..N-1; ld_rho >= lib_count.  (The
  *          library-major causal map of the paper is the transpose view.)
  *   ws     device workspace of at least edm_ccm_workspace_bytes(N, T, params)
- * This call synchronises `stream` once, to read optE on the host and plan
- * the target grouping; everything else is enqueued asynchronously.
+ * The grouping of targets by E is planned on the device, so the call does
+ * not synchronise and never reads optE back: launches are sized for the
+ * worst case and surplus blocks return at once.  A target whose optE is
+ * outside 1..EDM_MAX_E gets NaN in every column of its row.  Three cases
+ * plan on the host instead and synchronise `stream` once: EDM_FLAG_VALIDATE
+ * (optE is checked there; a bad value returns EDM_ERR_INVALID),
+ * EDM_FLAG_LOOKUP_SCALAR, and series too short for E = EDM_MAX_E (fewer
+ * than E+1 candidates beyond the exclusion window; a target of such an E
+ * returns EDM_ERR_INVALID).
  * Targets are staged in tiles of 32 (64 FP16) series; up to about 3,100
  * steps a tile sits in shared memory during the lookup, longer series (the
  * time-step sweep of the paper's Sec. IV reaches 40,000) read their tiles
@@ -150,8 +157,11 @@ size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params);
  *   rho   [n_lags][N][ld_rho] target-major per lag:
  *         rho[(l - lag_min) * N * ld_rho + j * ld_rho + i] = rho_l(i -> j)
  *   ws    edm_ccm_rho_lags_workspace_bytes(N, T, lag_min, lag_max, params)
- * Every E in optE needs E+1 candidates in its window, else EDM_ERR_INVALID.
- * Synchronises `stream` once (reads optE).
+ * Planned on the device like edm_ccm_rho (no synchronisation; an optE
+ * outside 1..EDM_MAX_E gives NaN rows in every lag).  When the lag window
+ * is too short for E = EDM_MAX_E, or with EDM_FLAG_VALIDATE, the call plans
+ * on the host (one synchronisation) and every E in optE must keep E+1
+ * candidates in its window, else EDM_ERR_INVALID.
  */
 int edm_ccm_rho_lags(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE, int32_t lag_min,
                      int32_t lag_max, const edm_params *params, float *rho, int64_t ld_rho, void *ws,
@@ -172,7 +182,10 @@ size_t edm_ccm_rho_lags_workspace_bytes(int64_t N, int64_t T, int32_t lag_min, i
  *   rho    [n_sub][N][ld_rho] target-major per subset
  *   ws     edm_ccm_workspace_bytes(N, T, params)
  * Each subset must leave E+1 candidates (beyond the exclusion window) for
- * the largest E in optE, else EDM_ERR_INVALID.  Synchronises `stream` once.
+ * the largest E in optE.  Planned on the device (no synchronisation): a
+ * subset that does not gets NaN in its whole plane.  With EDM_FLAG_VALIDATE
+ * (or series too short for E = EDM_MAX_E) the call plans on the host,
+ * synchronising once, and such a subset returns EDM_ERR_INVALID.
  */
 int edm_ccm_rho_subsets(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
                         const uint32_t *masks, int32_t n_sub, int64_t words, const edm_params *params, float *rho,
@@ -251,7 +264,9 @@ int edm_ccm_rho_batched_reset(void);
  *             ld_g >= N
  *   grad_Y    [N][ldY] float32, overwritten
  *   ws        at least edm_ccm_backward_workspace_bytes(N, T, params)
- * Requires T - Tp <= 3072.  Synchronises `stream` once (reads optE).
+ * Requires T - Tp <= 3072.  The E grouping is planned on the device (no
+ * synchronisation); a target whose optE is outside 1..EDM_MAX_E (or leaves
+ * fewer than E+1 candidates) contributes no gradient.
  * Summation order of the shared-memory accumulations varies between runs
  * (atomic adds), so the last bits of grad_Y may differ run to run.
  */
@@ -287,8 +302,8 @@ size_t edm_ccm_backward_workspace_bytes(int64_t N, int64_t T, const edm_params *
  *     exits.  All calls share it and it keeps the previous call's contents;
  *     calls whose GPU work overlaps (other streams, other host threads)
  *     race on it.
- *   - Like edm_ccm_rho it synchronises `stream` once (reading 84 bytes of
- *     per-E counts back to the host).
+ *   - It synchronises `stream` once (reading 84 bytes of per-E counts back
+ *     to the host).
  */
 int edm_ccm_rho_noalloc(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE,
                         int64_t lib_begin, int64_t lib_count, const edm_params *params,

@@ -191,7 +191,7 @@ def edm_ccm_rho_lags(Y: torch.Tensor, optE: torch.Tensor, lag_min: int, lag_max:
 def edm_ccm_rho_subsets(Y: torch.Tensor, optE: torch.Tensor, masks: torch.Tensor, tau: int = 1, Tp: int = 1,
                         exclusion_radius: int = 0, precision: int = EDM_PRECISION_FP32,
                         out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-                        stream=None) -> torch.Tensor:
+                        stream=None, flags: int = 0) -> torch.Tensor:
     """CCM convergence: out[u][j][i] = rho(library i -> target j) with each
     library's candidates restricted to subset u (masks: int32/uint32 CUDA
     tensor [n_sub][words], bit s = candidate time s allowed)."""
@@ -205,7 +205,7 @@ def edm_ccm_rho_subsets(Y: torch.Tensor, optE: torch.Tensor, masks: torch.Tensor
     n_sub, words = masks.shape
     if out is None:
         out = torch.empty((n_sub, N, N), dtype=torch.float32, device=Y.device)
-    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision)
+    p = make_params(tau=tau, Tp=Tp, exclusion_radius=exclusion_radius, precision=precision, flags=flags)
     need = int(lib.edm_ccm_workspace_bytes(N, T, ctypes.byref(p)))
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=Y.device)

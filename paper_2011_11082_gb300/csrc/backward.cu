@@ -63,6 +63,14 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
     const int E = a.optE[j], k = E + 1;
     const int L = (E - 1) * a.tau;
     const int Tq = a.T - a.Tp - L;
+    // a target whose E is unusable (outside 1..EDM_MAX_E, or too few
+    // candidates) has no rho and no gradient
+    if (E < 1 || E > EDM_MAX_E || Tq - (a.excl >= 0 ? 2 * a.excl + 1 : 0) < k) {
+        float *dst = a.grad_Y + (int64_t)j * a.ldY;
+        for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+            dst[t] += gy[t];
+        return;
+    }
     const double n = (double)Tq;
     // observation window statistics (once per target)
     double so = 0.0;

@@ -148,7 +148,7 @@ edm::TableLayout make_layout(uint32_t sel, int64_t T, const edm_params *p)
 }
 
 struct CcmWs {
-    size_t pi, omom, meta, tiles, tables, total;
+    size_t pi, omom, meta, tiles, tables, counts, slots, total;
     int64_t n_tiles_max;
     size_t table_bytes;  // L2-sized budget
     size_t table_cap;    // allocated table area
@@ -176,6 +176,12 @@ CcmWs ccm_ws_layout(int64_t N, int64_t T, const edm_params *p)
     off += align256((size_t)N * sizeof(float2));
     w.meta = off;
     off += align256((size_t)w.n_tiles_max * sizeof(edm::TileMeta));
+    // device-side plan: per-E counts and the launch slots (at most one per
+    // group and target block)
+    w.counts = off;
+    off += 256;
+    w.slots = off;
+    off += align256((size_t)edm::kMaxPlanGroups * (size_t)(w.n_tiles_max + 1) * sizeof(edm::SlotDesc));
     w.tiles = off;
     off += align256((size_t)w.n_tiles_max * (size_t)T * RB);
     w.tables = off;
@@ -395,8 +401,18 @@ size_t edm_ccm_workspace_bytes(int64_t N, int64_t T, const edm_params *params)
 
 namespace {
 
-// Host-side plan of the cross-map phase: targets grouped by E (stable),
-// tiles, and the device copies of the permutation and tile list.
+// A group of the device-side plan: targets of E in [elo, ehi] (static E
+// set `sel` for the table layout), tb_max target-block slots from slot0 on,
+// at most tiles_upper tiles per slot.
+struct DevGroup {
+    int elo, ehi;
+    uint32_t sel;
+    int slot0, tb_max, tiles_upper;
+};
+
+// Plan of the cross-map phase: targets grouped by E (stable) and tiles,
+// either planned on the host (tiles known here) or on the device (dev:
+// groups of fixed E ranges whose tile ranges live in slots_d).
 struct CcmPlan {
     std::vector<edm::TileMeta> tiles;
     int32_t *pi_d;
@@ -408,6 +424,10 @@ struct CcmPlan {
     bool l2;  // long series: tiles stay in global memory (FP32 only)
     int RB;
     CcmWs L;
+    bool dev = false;
+    std::vector<DevGroup> groups;
+    int32_t *counts_d = nullptr;
+    edm::SlotDesc *slots_d = nullptr;
 };
 
 int ccm_validate(int64_t N, int64_t T, int64_t ldY, const edm_params *params)
@@ -485,6 +505,124 @@ int ccm_prepare(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
     return EDM_OK;
 }
 
+// Whether every E in 1..EDM_MAX_E keeps E+1 candidates (queries and
+// candidates from s_lo on): then the device plan can take any optE without
+// a host check.
+bool all_E_usable(int64_t T, const edm_params *p, int64_t s_lo)
+{
+    for (int E = 1; E <= EDM_MAX_E; ++E) {
+        const int64_t A = std::max<int64_t>((int64_t)(E - 1) * p->tau, s_lo);
+        const int64_t cand = T - p->Tp - A - (p->exclusion_radius >= 0 ? 2 * (int64_t)p->exclusion_radius + 1 : 0);
+        if (cand < E + 1)
+            return false;
+    }
+    return true;
+}
+
+// The host plan (one synchronisation to read optE) serves EDM_FLAG_VALIDATE
+// (every optE checked, EDM_ERR_INVALID reported), the scalar comparison
+// lookup, and series too short for some E; everything else plans on the
+// device.
+bool host_plan_needed(int64_t T, const edm_params *p, int64_t s_lo)
+{
+    return (p->flags & (EDM_FLAG_VALIDATE | EDM_FLAG_LOOKUP_SCALAR)) != 0 || !all_E_usable(T, p, s_lo);
+}
+
+// Plan on the device from device optE (no host synchronisation): fixed
+// groups -- one over every E when all tiles fit one target block, else one
+// per E up to knn_thread_max_E() and one for the larger E, cut into target
+// blocks for long series -- whose tile ranges the plan kernel writes into
+// launch slots; targets with an unusable E get NaN rows (nan_* spec).  Then
+// stage the target tiles.
+int ccm_prepare_dev(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE_d, const edm_params *params,
+                    void *ws, cudaStream_t st, CcmPlan &P, int s_lo, float *nan_rho, int64_t ld_rho, int64_t row_len,
+                    int planes, int64_t plane_stride)
+{
+    P.L = ccm_ws_layout(N, T, params);
+    const CcmWs &L = P.L;
+    P.dev = true;
+    P.scalar = false;
+    P.RB = ccm_row_bytes(T, params);
+    P.l2 = edm::lookup_needs_l2((int)T);
+    P.want_f16 = params->precision == EDM_PRECISION_FP16_TARGETS && !P.l2;
+    unsigned char *wsb = (unsigned char *)ws;
+    P.pi_d = (int32_t *)(wsb + L.pi);
+    P.omom_d = (float2 *)(wsb + L.omom);
+    P.meta_d = (edm::TileMeta *)(wsb + L.meta);
+    P.tiles_d = (float *)(wsb + L.tiles);
+    P.tables_d = (uint8_t *)(wsb + L.tables);
+    P.counts_d = (int32_t *)(wsb + L.counts);
+    P.slots_d = (edm::SlotDesc *)(wsb + L.slots);
+    const int f16 = P.want_f16 ? 1 : 0;
+    const int n_tiles_max = (int)L.n_tiles_max;
+    const int tpb = (int)std::max<size_t>(1, kTileBlockBytes / ((size_t)T * P.RB));
+    P.groups.clear();
+    auto upper = [&](int elo, int ehi) {
+        int u = 0;
+        if (elo == ehi)
+            return (int)((N + edm::plan_tile_width(elo, f16, P.RB) - 1) / edm::plan_tile_width(elo, f16, P.RB));
+        u = (int)((N + P.RB / 4 - 1) / (P.RB / 4)) + (ehi - elo + 1);
+        return std::min(u, n_tiles_max);
+    };
+    if (n_tiles_max <= tpb) {
+        P.groups.push_back(DevGroup{1, EDM_MAX_E, (1u << EDM_MAX_E) - 1u, 0, 1, n_tiles_max});
+    } else {
+        const int thr = edm::knn_thread_max_E();
+        for (int E = 1; E <= thr; ++E)
+            P.groups.push_back(DevGroup{E, E, 1u << (E - 1), 0, 1, upper(E, E)});
+        uint32_t rare = 0;
+        for (int E = thr + 1; E <= EDM_MAX_E; ++E)
+            rare |= 1u << (E - 1);
+        P.groups.push_back(DevGroup{thr + 1, EDM_MAX_E, rare, 0, 1, upper(thr + 1, EDM_MAX_E)});
+    }
+    edm::CcmPlanSpec sp{};
+    sp.N = (int)N;
+    sp.T = (int)T;
+    sp.tau = params->tau;
+    sp.Tp = params->Tp;
+    sp.excl = params->exclusion_radius;
+    sp.s_lo = s_lo;
+    sp.f16 = f16;
+    sp.RB = P.RB;
+    sp.n_tiles_max = n_tiles_max;
+    sp.n_groups = (int)P.groups.size();
+    sp.tiles_per_block = P.l2 ? tpb : 0;
+    int slot = 0;
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+        DevGroup &G = P.groups[g];
+        if (P.l2) {
+            G.tb_max = (G.tiles_upper + tpb - 1) / tpb;
+            G.tiles_upper = std::min(G.tiles_upper, tpb);
+        }
+        G.slot0 = slot;
+        slot += G.tb_max;
+        sp.g_lo[g] = G.elo;
+        sp.g_hi[g] = G.ehi;
+        sp.tb_max[g] = G.tb_max;
+        sp.slot0[g] = G.slot0;
+    }
+    if ((size_t)slot > (size_t)edm::kMaxPlanGroups * (size_t)(L.n_tiles_max + 1))
+        return EDM_ERR_UNSUPPORTED;
+    sp.rho = nan_rho;
+    sp.ld_rho = ld_rho;
+    sp.row_len = row_len;
+    sp.planes = planes;
+    sp.plane_stride = plane_stride;
+    {
+        LaunchScope ls(EDM_KERNEL_PLAN, st, (double)N);
+        EDM_CUDA(edm::launch_ccm_plan(optE_d, sp, P.counts_d, P.pi_d, P.meta_d, P.slots_d, st));
+    }
+    {
+        LaunchScope ls(EDM_KERNEL_PREP, st, (double)N);
+        EDM_CUDA(edm::launch_prep_targets(Y, ldY, (int)T, params->tau, params->Tp, P.pi_d, P.meta_d, n_tiles_max,
+                                          P.tiles_d, P.omom_d, st, P.RB));
+        if (P.want_f16)
+            EDM_CUDA(edm::launch_prep_targets_f16(Y, ldY, (int)T, params->tau, params->Tp, P.pi_d, P.meta_d,
+                                                  n_tiles_max, (uint8_t *)P.tiles_d, P.omom_d, st, P.RB));
+    }
+    return EDM_OK;
+}
+
 // Time-delay form: lags lag_min .. lag_min + n_lags - 1 cross-mapped from the
 // same tables (queries and candidates from s_lo on); omom holds the
 // observation sums of each lag ([n_lags][N]); lag l writes rho + l * stride.
@@ -519,6 +657,11 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
     edm::TileMeta *meta_d = P.meta_d;
     float *tiles_d = P.tiles_d;
     uint8_t *tables_d = P.tables_d;
+    const int sms = sm_count();
+    // shared-memory tiles: at least ~16 CTAs per SM in all (one CTA per SM
+    // is resident), so the last wave is a small tail; tiles in L2: 4 per SM
+    // per register class
+    const int want = (P.l2 ? 4 : 16) * sms;
     // --- target groups x library blocks ----------------------------------------
     // One group per E up to knn_thread_max_E() (the tables of that E, one
     // build per library), the larger E together (one warp-kernel sweep
@@ -527,37 +670,56 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
     // group's tiles stream through shared memory.  Tiles read from L2 (long
     // series): a group is further cut into L2-sized target blocks, so its
     // tiles stay resident while every library block sweeps them.
-    const size_t tile_bytes = (size_t)T * P.RB;
-    const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
-    const int sms = sm_count();
-    std::vector<std::pair<int, int>> groups;  // tile ranges [first, last)
-    // all tiles within one target block: one group, so one warp-kernel
-    // sweep serves every E (no table is built twice either way; per-E
-    // thread launches measured slower there: 28.7 vs 26.5 ms per step at
-    // N = 1,000, T = 1,000)
-    if (n_tiles <= tiles_per_block)
-        groups.emplace_back(0, n_tiles);
-    for (int t0 = groups.empty() ? 0 : n_tiles; t0 < n_tiles;) {
-        const int E = tiles[(size_t)t0].E;
-        int t1 = t0 + 1;
-        if (E <= edm::knn_thread_max_E())
-            while (t1 < n_tiles && tiles[(size_t)t1].E == E)
-                ++t1;
-        else
-            t1 = n_tiles;
-        if (P.l2)
-            for (int b = t0; b < t1; b += tiles_per_block)
-                groups.emplace_back(b, std::min(t1, b + tiles_per_block));
-        else
-            groups.emplace_back(t0, t1);
-        t0 = t1;
+    struct LaunchGroup {
+        uint32_t sel;                  // E set of the table layout
+        int tb0, ntb;                  // host plan: tile range
+        const edm::SlotDesc *slot;     // device plan: the slot
+        int grid;                      // device plan: upper-bound grid
+        bool first;                    // device plan: carries the launch's pair count
+    };
+    std::vector<LaunchGroup> groups;
+    if (P.dev) {
+        for (size_t g = 0; g < P.groups.size(); ++g) {
+            const DevGroup &G = P.groups[g];
+            for (int tb = 0; tb < G.tb_max; ++tb)
+                groups.push_back(LaunchGroup{G.sel, 0, 0, P.slots_d + G.slot0 + tb,
+                                             G.tiles_upper + (P.l2 ? 2 : 1) * want, g == 0 && tb == 0});
+        }
+    } else {
+        const size_t tile_bytes = (size_t)T * P.RB;
+        const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
+        std::vector<std::pair<int, int>> ranges;  // tile ranges [first, last)
+        // all tiles within one target block: one group, so one warp-kernel
+        // sweep serves every E (no table is built twice either way; per-E
+        // thread launches measured slower there: 28.7 vs 26.5 ms per step at
+        // N = 1,000, T = 1,000)
+        if (n_tiles <= tiles_per_block)
+            ranges.emplace_back(0, n_tiles);
+        for (int t0 = ranges.empty() ? 0 : n_tiles; t0 < n_tiles;) {
+            const int E = tiles[(size_t)t0].E;
+            int t1 = t0 + 1;
+            if (E <= edm::knn_thread_max_E())
+                while (t1 < n_tiles && tiles[(size_t)t1].E == E)
+                    ++t1;
+            else
+                t1 = n_tiles;
+            if (P.l2)
+                for (int b = t0; b < t1; b += tiles_per_block)
+                    ranges.emplace_back(b, std::min(t1, b + tiles_per_block));
+            else
+                ranges.emplace_back(t0, t1);
+            t0 = t1;
+        }
+        for (const auto &r : ranges) {
+            uint32_t sel = 0;
+            for (int t = r.first; t < r.second; ++t)
+                sel |= 1u << (tiles[(size_t)t].E - 1);
+            groups.push_back(LaunchGroup{sel, r.first, r.second - r.first, nullptr, 0, false});
+        }
     }
     for (const auto &g : groups) {
-        const int tb0 = g.first;
-        const int ntb = g.second - g.first;
-        uint32_t sel = 0;
-        for (int t = tb0; t < tb0 + ntb; ++t)
-            sel |= 1u << (tiles[(size_t)t].E - 1);
+        const uint32_t sel = g.sel;
+        const uint32_t *sel_dev = g.slot ? &g.slot->sel : nullptr;
         const edm::TableLayout lay = make_layout(sel, T, params);
         // L2-sized library blocks; blocks of rare-E target blocks (many E,
         // few tiles) may spill to HBM rather than shrink below kMinLibBlock
@@ -572,18 +734,26 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
                 LaunchScope ls(EDM_KERNEL_KNN, st, (double)nlb * __builtin_popcount(sel), 0);
                 if (subsets)  // candidate subsets: the warp kernel (mask test per candidate)
                     EDM_CUDA(edm::launch_knn_tables(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau, params->Tp,
-                                                    params->exclusion_radius, sel, lay, tables_d, st, 64, nullptr, 0,
+                                                    params->exclusion_radius, sel, lay, tables_d, st, 64, sel_dev, 0,
                                                     subsets->masks + (size_t)su * subsets->words));
                 else
                     EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lib_begin + lb0, nlb, (int)T, params->tau,
                                                          params->Tp, params->exclusion_radius, sel, lay, tables_d, st,
                                                          (params->flags & EDM_FLAG_KNN_WARP) != 0,
-                                                         lags ? lags->s_lo : 0, &n_knn));
+                                                         lags ? lags->s_lo : 0, &n_knn, sel_dev));
                 ls.add_launches(EDM_KERNEL_KNN, n_knn);
             }
-            int64_t targets = 0;
-            for (int t = tb0; t < tb0 + ntb; ++t)
-                targets += tiles[(size_t)t].count;
+            // pairs of this launch (device plan: the whole block's N x nlb is
+            // counted on the first group's launches)
+            double pairs = 0.0;
+            if (g.slot) {
+                pairs = g.first ? (double)N * (double)nlb : 0.0;
+            } else {
+                int64_t targets = 0;
+                for (int t = g.tb0; t < g.tb0 + g.ntb; ++t)
+                    targets += tiles[(size_t)t].count;
+                pairs = (double)targets * (double)nlb;
+            }
             edm::LookupArgs a;
             a.tiles = tiles_d;
             a.meta = meta_d;
@@ -601,12 +771,12 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
             a.rho = subsets ? rho + su * subsets->rho_stride : rho;
             a.ld_rho = ld_rho;
             if (scalar) {
-                // comparison path: one launch per run of equal E
-                for (int r0 = tb0; r0 < tb0 + ntb;) {
+                // comparison path (host plan only): one launch per run of equal E
+                for (int r0 = g.tb0; r0 < g.tb0 + g.ntb;) {
                     const int E = tiles[(size_t)r0].E;
                     int r1 = r0;
                     int64_t tg = 0;
-                    while (r1 < tb0 + ntb && tiles[(size_t)r1].E == E)
+                    while (r1 < g.tb0 + g.ntb && tiles[(size_t)r1].E == E)
                         tg += tiles[(size_t)r1++].count;
                     a.tile_begin = r0;
                     a.n_tiles = r1 - r0;
@@ -617,19 +787,24 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
                     r0 = r1;
                 }
             } else {
-                a.tile_begin = tb0;
-                a.n_tiles = ntb;
-                // shared-memory tiles: at least ~16 CTAs per SM in all (one
-                // CTA per SM is resident), so the last wave is a small tail
-                const int want = (P.l2 ? 4 : 16) * sms;
-                int parts = (want + ntb - 1) / ntb;
-                a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
-                const int n_lk = lags ? lags->n_lags : 1;
-                // tiles read from L2: one launch per register class present
                 int n_small = 0;
-                while (P.l2 && n_small < ntb && tiles[(size_t)(tb0 + n_small)].E + 1 <= edm::kL2SplitK)
-                    ++n_small;
-                const int lk_launches = P.l2 ? (n_small > 0) + (ntb - n_small > 0) : 1;
+                if (g.slot) {
+                    a.slot = g.slot;
+                    a.want = want;
+                    a.tile_begin = 0;
+                    a.n_tiles = g.grid;
+                    a.lib_parts = 1;
+                } else {
+                    a.tile_begin = g.tb0;
+                    a.n_tiles = g.ntb;
+                    int parts = (want + g.ntb - 1) / g.ntb;
+                    a.lib_parts = std::max(1, std::min(parts, (nlb + 7) / 8));
+                    // tiles read from L2: one launch per register class present
+                    while (P.l2 && n_small < g.ntb && tiles[(size_t)(g.tb0 + n_small)].E + 1 <= edm::kL2SplitK)
+                        ++n_small;
+                }
+                const int n_lk = lags ? lags->n_lags : 1;
+                const int lk_launches = !P.l2 ? 1 : (g.slot ? 2 : (n_small > 0) + (g.ntb - n_small > 0));
                 for (int li = 0; li < n_lk; ++li) {
                     if (lags) {
                         a.s_lo = lags->s_lo;
@@ -637,7 +812,7 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
                         a.omom = lags->omom + (size_t)li * N;
                         a.rho = rho + li * lags->rho_stride;
                     }
-                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, (double)targets * (double)nlb, lk_launches);
+                    LaunchScope ls(EDM_KERNEL_LOOKUP, st, pairs, lk_launches);
                     if (P.l2) {
                         EDM_CUDA(edm::launch_lookup_l2(a, n_small, sms, st));
                     } else {
@@ -672,11 +847,15 @@ int edm_ccm_rho(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t
     if (lib_count == 0)
         return EDM_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<int32_t> E_host((size_t)N);
-    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    EDM_CUDA(cudaStreamSynchronize(st));
     CcmPlan P;
-    rc = ccm_prepare(Y, N, T, ldY, E_host.data(), params, ws, st, P);
+    if (host_plan_needed(T, params, 0)) {
+        std::vector<int32_t> E_host((size_t)N);
+        EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        EDM_CUDA(cudaStreamSynchronize(st));
+        rc = ccm_prepare(Y, N, T, ldY, E_host.data(), params, ws, st, P);
+    } else {
+        rc = ccm_prepare_dev(Y, N, T, ldY, optE, params, ws, st, P, 0, rho, ld_rho, lib_count, 1, 0);
+    }
     if (rc)
         return rc;
     return ccm_execute(P, Y, N, T, ldY, lib_begin, lib_count, params, rho, ld_rho, st);
@@ -715,30 +894,35 @@ int edm_ccm_rho_lags(const float *Y, int64_t N, int64_t T, int64_t ldY, const in
     if ((rc = validate_series(Y, N, T, ldY, &pe, (cudaStream_t)stream)) != EDM_OK)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<int32_t> E_host((size_t)N);
-    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    EDM_CUDA(cudaStreamSynchronize(st));
-    for (int64_t j = 0; j < N; ++j) {  // every lag's window must hold k neighbours
-        const int E = E_host[(size_t)j];
-        if (E < 1 || E > EDM_MAX_E)
-            return EDM_ERR_INVALID;
-        const int64_t A = std::max<int64_t>((int64_t)(E - 1) * pe.tau, s_lo);
-        int64_t cand = (T - pe.Tp) - A;
-        if (pe.exclusion_radius >= 0)
-            cand -= 2 * (int64_t)pe.exclusion_radius + 1;
-        if (cand < E + 1)
-            return EDM_ERR_INVALID;
-    }
     CcmPlan P;
-    rc = ccm_prepare(Y, N, T, ldY, E_host.data(), &pe, ws, st, P);
+    if (host_plan_needed(T, &pe, s_lo)) {
+        std::vector<int32_t> E_host((size_t)N);
+        EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        EDM_CUDA(cudaStreamSynchronize(st));
+        for (int64_t j = 0; j < N; ++j) {  // every lag's window must hold k neighbours
+            const int E = E_host[(size_t)j];
+            if (E < 1 || E > EDM_MAX_E)
+                return EDM_ERR_INVALID;
+            const int64_t A = std::max<int64_t>((int64_t)(E - 1) * pe.tau, s_lo);
+            int64_t cand = (T - pe.Tp) - A;
+            if (pe.exclusion_radius >= 0)
+                cand -= 2 * (int64_t)pe.exclusion_radius + 1;
+            if (cand < E + 1)
+                return EDM_ERR_INVALID;
+        }
+        rc = ccm_prepare(Y, N, T, ldY, E_host.data(), &pe, ws, st, P);
+    } else {
+        rc = ccm_prepare_dev(Y, N, T, ldY, optE, &pe, ws, st, P, s_lo, rho, ld_rho, N, n_lags, N * ld_rho);
+    }
     if (rc)
         return rc;
     float2 *omom_l = (float2 *)((unsigned char *)ws + base);
+    const int n_tiles_l = P.dev ? (int)P.L.n_tiles_max : (int)P.tiles.size();
     {
         LaunchScope ls(EDM_KERNEL_PREP, st, (double)N * n_lags, n_lags);
         for (int li = 0; li < n_lags; ++li)
-            EDM_CUDA(edm::launch_obs_moments(P.tiles_d, P.RB, P.meta_d, (int)P.tiles.size(), (int)T, pe.tau, pe.Tp,
-                                             s_lo, lag_min + li, omom_l + (size_t)li * N, st));
+            EDM_CUDA(edm::launch_obs_moments(P.tiles_d, P.RB, P.meta_d, n_tiles_l, (int)T, pe.tau, pe.Tp, s_lo,
+                                             lag_min + li, omom_l + (size_t)li * N, st));
     }
     LagSpec spec{lag_min, n_lags, s_lo, omom_l, N * ld_rho};
     return ccm_execute(P, Y, N, T, ldY, 0, N, &pe, rho, ld_rho, st, &spec);
@@ -760,6 +944,20 @@ int edm_ccm_rho_subsets(const float *Y, int64_t N, int64_t T, int64_t ldY, const
     if ((rc = validate_series(Y, N, T, ldY, params, (cudaStream_t)stream)) != EDM_OK)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    SubsetSpec spec{masks, n_sub, words, N * ld_rho};
+    if (!host_plan_needed(T, params, 0)) {
+        // planned on the device; a subset that leaves too few candidates for
+        // the largest E in use gets a NaN plane afterwards
+        CcmPlan P;
+        rc = ccm_prepare_dev(Y, N, T, ldY, optE, params, ws, st, P, 0, rho, ld_rho, N, n_sub, N * ld_rho);
+        if (rc)
+            return rc;
+        if ((rc = ccm_execute(P, Y, N, T, ldY, 0, N, params, rho, ld_rho, st, nullptr, &spec)) != EDM_OK)
+            return rc;
+        EDM_CUDA(edm::launch_subset_check(masks, n_sub, words, P.counts_d, (int)N, (int)T, params->tau, params->Tp,
+                                          params->exclusion_radius, rho, ld_rho, N * ld_rho, st));
+        return EDM_OK;
+    }
     std::vector<int32_t> E_host((size_t)N);
     std::vector<uint32_t> m_host((size_t)n_sub * (size_t)words);
     EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -786,7 +984,6 @@ int edm_ccm_rho_subsets(const float *Y, int64_t N, int64_t T, int64_t ldY, const
     rc = ccm_prepare(Y, N, T, ldY, E_host.data(), params, ws, st, P);
     if (rc)
         return rc;
-    SubsetSpec spec{masks, n_sub, words, N * ld_rho};
     return ccm_execute(P, Y, N, T, ldY, 0, N, params, rho, ld_rho, st, nullptr, &spec);
 }
 
@@ -894,7 +1091,8 @@ namespace {
 constexpr size_t kBwTableBytes = 256ull << 20;
 
 struct BwWs {
-    size_t pi, e_start, obar, stats, tables, table_bytes, total;
+    size_t pi, e_start, counts, meta, obar, stats, tables, table_bytes, total;
+    int64_t n_tiles_max;
 };
 
 BwWs bw_layout(int64_t N, int64_t T, const edm_params *p)
@@ -905,6 +1103,13 @@ BwWs bw_layout(int64_t N, int64_t T, const edm_params *p)
     off += align256((size_t)N * 4);
     w.e_start = off;
     off += 256;
+    // device-side plan (counts, and the tile list the plan kernel writes
+    // for 32-target tiles)
+    w.counts = off;
+    off += 256;
+    w.n_tiles_max = (N + 31) / 32 + EDM_MAX_E;
+    w.meta = off;
+    off += align256((size_t)w.n_tiles_max * sizeof(edm::TileMeta));
     w.obar = off;
     off += align256((size_t)N * 4);
     w.stats = off;
@@ -940,33 +1145,34 @@ int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, cons
     if (ws_bytes < L.total)
         return EDM_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<int32_t> E_host((size_t)N);
-    EDM_CUDA(cudaMemcpyAsync(E_host.data(), optE, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
-    EDM_CUDA(cudaStreamSynchronize(st));
-    int32_t start[EDM_MAX_E + 2] = {0};
-    int64_t count[EDM_MAX_E + 2] = {0};
-    uint32_t sel = 0;
-    int kmax = 2;
-    for (int64_t j = 0; j < N; ++j) {
-        int E = E_host[(size_t)j];
-        if (E < 1 || E > EDM_MAX_E || ccm_min_candidates(T, E, params) < E + 1)
-            return EDM_ERR_INVALID;
-        count[E]++;
-        sel |= 1u << (E - 1);
-        kmax = std::max(kmax, E + 1);
-    }
-    for (int E = 1; E <= EDM_MAX_E; ++E)
-        start[E + 1] = start[E] + (int32_t)count[E];
-    std::vector<int32_t> pi((size_t)N);
-    {
-        int32_t fill[EDM_MAX_E + 2];
-        memcpy(fill, start, sizeof fill);
-        for (int64_t j = 0; j < N; ++j)
-            pi[(size_t)fill[E_host[(size_t)j]]++] = (int32_t)j;
-    }
     unsigned char *wsb = (unsigned char *)ws;
-    EDM_CUDA(cudaMemcpyAsync(wsb + L.pi, pi.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
-    EDM_CUDA(cudaMemcpyAsync(wsb + L.e_start, start, sizeof start, cudaMemcpyHostToDevice, st));
+    // the target permutation by E and the E ranges, planned on the device
+    // (targets whose E is unusable are left out: no rho, no gradient)
+    {
+        edm::CcmPlanSpec sp{};
+        sp.N = (int)N;
+        sp.T = (int)T;
+        sp.tau = params->tau;
+        sp.Tp = params->Tp;
+        sp.excl = params->exclusion_radius;
+        sp.f16 = 0;
+        sp.RB = 128;
+        sp.n_tiles_max = (int)L.n_tiles_max;
+        sp.n_groups = 1;  // one slot: the E in use, for the kNN sweep
+        sp.g_lo[0] = 1;
+        sp.g_hi[0] = EDM_MAX_E;
+        sp.tb_max[0] = 1;
+        sp.slot0[0] = 0;
+        sp.starts = (int32_t *)(wsb + L.e_start);
+        LaunchScope ls(EDM_KERNEL_PLAN, st, (double)N);
+        EDM_CUDA(edm::launch_ccm_plan(optE, sp, (int32_t *)(wsb + L.counts), (int32_t *)(wsb + L.pi),
+                                      (edm::TileMeta *)(wsb + L.meta), (edm::SlotDesc *)(wsb + L.counts + 128), st));
+    }
+    // tables for every E in the layout; the kNN sweep builds only the E in
+    // use (device mask)
+    const uint32_t sel = (1u << EDM_MAX_E) - 1u;
+    const uint32_t *sel_dev = &((const edm::SlotDesc *)(wsb + L.counts + 128))->sel;
+    const int kmax = EDM_MAX_E + 1;
     EDM_CUDA(cudaMemset2DAsync(grad_Y, (size_t)ldY * 4, 0, (size_t)T * 4, (size_t)N, st));
     const edm::TableLayout lay = make_layout(sel, T, params);
     const int64_t per_block =
@@ -978,7 +1184,7 @@ int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, cons
             int n_knn = 1;
             EDM_CUDA(edm::launch_knn_tables_auto(Y, ldY, lb0, nlb, (int)T, params->tau, params->Tp,
                                                  params->exclusion_radius, sel, lay, wsb + L.tables, st,
-                                                 (params->flags & EDM_FLAG_KNN_WARP) != 0, 0, &n_knn));
+                                                 (params->flags & EDM_FLAG_KNN_WARP) != 0, 0, &n_knn, sel_dev));
             ls.add_launches(EDM_KERNEL_KNN, n_knn - 1);
         }
         edm::BwArgs a;
@@ -987,6 +1193,7 @@ int edm_ccm_rho_backward(const float *Y, int64_t N, int64_t T, int64_t ldY, cons
         a.T = (int)T;
         a.tau = params->tau;
         a.Tp = params->Tp;
+        a.excl = params->exclusion_radius;
         a.optE = optE;
         a.grad_rho = grad_rho;
         a.ld_g = ld_g;

@@ -403,17 +403,17 @@ static bool use_thread_kernel(int tau, uint32_t sel, bool force_warp)
 
 cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp,
                                    int excl, uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
-                                   bool force_warp, int s_lo, int *n_launches)
+                                   bool force_warp, int s_lo, int *n_launches, const uint32_t *sel_dev)
 {
     const bool thread = use_thread_kernel(tau, sel, force_warp);
     if (n_launches)
         *n_launches = thread ? __builtin_popcount(sel) : 1;
     if (!thread)
-        return launch_knn_tables(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, st, 64, nullptr, s_lo);
+        return launch_knn_tables(Y, ldY, lib0, n_lib, T, tau, Tp, excl, sel, lay, tables, st, 64, sel_dev, s_lo);
     for (int E = 1; E <= 32 - __builtin_clz(sel); ++E) {
         if (!((sel >> (E - 1)) & 1u))
             continue;
-        cudaError_t e = launch_knn_thread(Y, ldY, lib0, n_lib, T, Tp, excl, E, lay, tables, st, nullptr, s_lo);
+        cudaError_t e = launch_knn_thread(Y, ldY, lib0, n_lib, T, Tp, excl, E, lay, tables, st, sel_dev, s_lo);
         if (e != cudaSuccess)
             return e;
     }

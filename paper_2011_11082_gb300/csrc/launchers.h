@@ -50,9 +50,11 @@ cudaError_t knn_thread_counters(unsigned long long out[2], bool reset);
 // Tables for the E set `sel` with the cheaper kernel by a measured cost
 // model: thread-per-query launches (one per E, all E <= knn_thread_max_E(),
 // tau = 1) or one warp-kernel launch.  Returns the launches made in *n.
+// sel_dev (optional): device E mask ANDed into sel.
 cudaError_t launch_knn_tables_auto(const float *Y, int64_t ldY, int64_t lib0, int n_lib, int T, int tau, int Tp,
                                    int excl, uint32_t sel, const TableLayout &lay, uint8_t *tables, cudaStream_t st,
-                                   bool force_warp = false, int s_lo = 0, int *n_launches = nullptr);
+                                   bool force_warp = false, int s_lo = 0, int *n_launches = nullptr,
+                                   const uint32_t *sel_dev = nullptr);
 
 // FP64 re-rank / exhaustive-scan query counts of the kNN kernels on the
 // current device (synchronises); reset clears them.
@@ -88,6 +90,50 @@ cudaError_t launch_prep_targets(const float *Y, int64_t ldY, int T, int tau, int
                                 const TileMeta *meta, int n_tiles, float *tiles, float2 *omom, cudaStream_t st,
                                 int RB = 128);
 
+// Device-planned launch slot: a tile range and the E it contains.
+struct SlotDesc {
+    int tile_begin;
+    int n_tiles;
+    uint32_t sel;  // bit E-1: E present in the range
+    int pad;
+};
+
+// Tiles per E: FP16 tiles hold 2x the targets of FP32 tiles (RB/2 vs RB/4).
+__host__ __device__ inline int plan_tile_width(int E, int f16, int RB)
+{
+    return (f16 && E + 1 <= kF16MaxK) ? RB / 2 : RB / 4;
+}
+
+constexpr int kMaxPlanGroups = 8;
+
+// Inputs of the device-side plan (ccm_plan.cu).
+struct CcmPlanSpec {
+    int N, T, tau, Tp, excl;
+    int s_lo;             // first query/candidate time (time-delay form), else 0
+    int f16, RB;          // FP16 tiles for E + 1 <= kF16MaxK when f16; tile row bytes
+    int n_tiles_max;      // tile slots to fill (unused ones get E = 0)
+    int n_groups;         // groups of E ranges, in tile order
+    int g_lo[kMaxPlanGroups], g_hi[kMaxPlanGroups];
+    int tiles_per_block;  // target-block cut of each group (0: none)
+    int tb_max[kMaxPlanGroups];
+    int slot0[kMaxPlanGroups];  // first slot of each group
+    // NaN rows for targets whose E is unusable: rho + u*plane_stride +
+    // j*ld_rho, row_len values, for u < planes (rho null: none)
+    float *rho;
+    int64_t ld_rho, row_len, plane_stride;
+    int planes;
+    int32_t *starts;  // optional: first sorted position of each E (E = 0..EDM_MAX_E+1)
+};
+
+// counts[0]: targets with an unusable E; counts[E]: targets of E;
+// counts[EDM_MAX_E + 1]: tiles in use.  pi: target indices sorted by E.
+cudaError_t launch_ccm_plan(const int32_t *optE, const CcmPlanSpec &sp, int32_t *counts, int32_t *pi, TileMeta *meta,
+                            SlotDesc *slots, cudaStream_t st);
+// NaN planes for convergence subsets that leave too few candidates.
+cudaError_t launch_subset_check(const uint32_t *masks, int n_sub, int64_t words, const int32_t *counts, int N, int T,
+                                int tau, int Tp, int excl, float *rho, int64_t ld_rho, int64_t plane_stride,
+                                cudaStream_t st);
+
 struct LookupArgs {
     const float *tiles;
     const TileMeta *meta;
@@ -108,7 +154,36 @@ struct LookupArgs {
     // lag = Tp (chunked kernels only).
     int s_lo;
     int lag;
+    // device-planned launch (chunked and L2 kernels): the tile range comes
+    // from *slot, the library split is chosen in the kernel for about `want`
+    // CTAs, and the 1-D grid is an upper bound (surplus CTAs return).
+    // slot == nullptr: tile_begin / n_tiles / lib_parts as given, grid
+    // (n_tiles, lib_parts).  With a slot, n_tiles is the grid size.
+    const SlotDesc *slot = nullptr;
+    int want = 0;
 };
+
+// (tile, library part) of this CTA, or false when the CTA has no work.
+__device__ __forceinline__ bool lookup_item(const LookupArgs &a, int &tile, int &part, int &parts)
+{
+    if (a.slot) {
+        const int ntb = a.slot->n_tiles;
+        if (ntb <= 0)
+            return false;
+        parts = (a.want + ntb - 1) / ntb;
+        const int cap = (a.n_lib + 7) / 8;
+        parts = parts < 1 ? 1 : (parts > cap ? cap : parts);
+        if ((int)blockIdx.x >= ntb * parts)
+            return false;
+        tile = a.slot->tile_begin + (int)blockIdx.x / parts;
+        part = (int)blockIdx.x % parts;
+        return true;
+    }
+    tile = a.tile_begin + (int)blockIdx.x;
+    part = (int)blockIdx.y;
+    parts = a.lib_parts;
+    return true;
+}
 
 // Observation sums (S_o, n S_oo - S_o^2) of every staged target at lag
 // `lag` over the query times max((E-1)tau, s_lo) .. T-1-Tp of its tile's E,
@@ -152,7 +227,7 @@ void prof_push(int kernel, cudaEvent_t a, cudaEvent_t b, double units);
 struct BwArgs {
     const float *Y;
     int64_t ldY;
-    int T, tau, Tp;
+    int T, tau, Tp, excl;
     const int32_t *optE;
     const float *grad_rho;
     int64_t ld_g;

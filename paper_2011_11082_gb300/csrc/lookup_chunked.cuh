@@ -409,7 +409,7 @@ __device__ __forceinline__ void chunk_shifts(const float *red, int c0, float *sh
 // kLag: the time-delay form (tables over t >= s_lo, lag shift); the plain
 // instantiation folds those terms away (s_lo = 0, lag = Tp).
 template <int K, bool F16, int RB, bool kLag = false>
-__device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
+__device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a, int tile, int part, int parts)
 {
     // RB-byte rows hold RB/16 chunks; FP32 chunks are 4 targets, FP16 chunks
     // 4 words = 8 targets (word w = targets w and w + RB/4).  FP16 with
@@ -428,7 +428,6 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
     unsigned char *smem = smem_raw + pad;
     float *red_all = reinterpret_cast<float *>(smem + (size_t)a.T * RB);
 
-    const int tile = a.tile_begin + blockIdx.x;
     const TileMeta m = a.meta[tile];
     const int E = K - 1;
     CkRows cx;
@@ -464,8 +463,8 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a)
 
     const int lane = lane_id(), warp = warp_id();
     float *red = red_all + warp * 32 * kCkRed;
-    const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
-    const int lib_lo = blockIdx.y * per;
+    const int per = (a.n_lib + parts - 1) / parts;
+    const int lib_lo = part * per;
     const int lib_hi = min(a.n_lib, lib_lo + per);
     cx.lane16 = (uint32_t)lane_sub<RB>(lane) * 16u;
 

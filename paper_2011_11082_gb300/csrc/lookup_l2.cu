@@ -45,9 +45,8 @@ __device__ __forceinline__ float4 ldg_v4(const float4 *p)
 // kLag: the time-delay form (tables over t >= s_lo; gathers at the stored
 // neighbour time shifted by lag - Tp, observations at t + lag).
 template <int K, bool kLag>
-__device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
+__device__ __forceinline__ void lookup_l2_body(const LookupArgs &a, int tile, int part, int parts)
 {
-    const int tile = a.tile_begin + blockIdx.x;
     const TileMeta m = a.meta[tile];
     const int E = K - 1;
     const int L = (E - 1) * a.tau;
@@ -62,8 +61,8 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
     const float4 *tl = reinterpret_cast<const float4 *>(a.tiles) + (size_t)tile * a.T * 8;
     const int lane = lane_id(), warp = warp_id();
     const int grp = lane >> 3, sub = lane & 7;
-    const int per = (a.n_lib + a.lib_parts - 1) / a.lib_parts;
-    const int lib_lo = blockIdx.y * per;
+    const int per = (a.n_lib + parts - 1) / parts;
+    const int lib_lo = part * per;
     const int lib_hi = min(a.n_lib, lib_lo + per);
     const size_t tq_pad = (size_t)a.lay.Tq_pad;
     const float4 *tsub = tl + sub;
@@ -195,12 +194,15 @@ __device__ __forceinline__ void lookup_l2_body(const LookupArgs &a)
 template <bool kLag, bool kLarge>
 __global__ void __launch_bounds__(kL2Threads, kLarge ? 1 : 2) lookup_l2_kernel(LookupArgs a)
 {
-    const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
+    int tile, part, parts;
+    if (!lookup_item(a, tile, part, parts))
+        return;
+    const TileMeta m = a.meta[tile];
     const int K = m.E + 1;
     if (K < 2 || (K > kL2SplitK) != kLarge)
         return;
 #define EDM_L2(KK)                                                                                                     \
-    case KK: lookup_l2_body<KK, kLag>(a); break;
+    case KK: lookup_l2_body<KK, kLag>(a, tile, part, parts); break;
     if (!kLarge) {
         switch (K) {
             EDM_L2(2)
@@ -239,16 +241,24 @@ cudaError_t launch_lookup_l2(const LookupArgs &a, int n_small, int sms, cudaStre
         return cudaSuccess;
     const bool lag = a.s_lo != 0 || a.lag != a.Tp;
     // each class gets its own library split, sized so that its tiles alone
-    // fill the GPU (two resident CTAs per SM for small K, one for large K)
+    // fill the GPU (two resident CTAs per SM for small K, one for large K);
+    // device-planned slots: both launches span the slot's tiles (a CTA of
+    // the other class returns), the split sized for the slot
     for (int large = 0; large < 2; ++large) {
         LookupArgs b = a;
-        b.tile_begin = a.tile_begin + (large ? n_small : 0);
-        b.n_tiles = large ? a.n_tiles - n_small : n_small;
-        if (b.n_tiles <= 0)
-            continue;
-        const int want = 4 * sms * (large ? 1 : 2);
-        b.lib_parts = std::max(1, std::min((want + b.n_tiles - 1) / b.n_tiles, (a.n_lib + 7) / 8));
-        dim3 grid((unsigned)b.n_tiles, (unsigned)b.lib_parts);
+        dim3 grid;
+        if (a.slot) {
+            grid = dim3((unsigned)a.n_tiles);
+            b.want = a.want * (large ? 1 : 2);
+        } else {
+            b.tile_begin = a.tile_begin + (large ? n_small : 0);
+            b.n_tiles = large ? a.n_tiles - n_small : n_small;
+            if (b.n_tiles <= 0)
+                continue;
+            const int want = 4 * sms * (large ? 1 : 2);
+            b.lib_parts = std::max(1, std::min((want + b.n_tiles - 1) / b.n_tiles, (a.n_lib + 7) / 8));
+            grid = dim3((unsigned)b.n_tiles, (unsigned)b.lib_parts);
+        }
         if (lag) {
             if (large)
                 lookup_l2_kernel<true, true><<<grid, kL2Threads, 0, st>>>(b);

@@ -13,14 +13,17 @@ namespace edm {
 // specialisation's code.
 __global__ void __launch_bounds__(kCkThreads, 1) EDM_MULTI_NAME(LookupArgs a)
 {
-    const TileMeta m = a.meta[a.tile_begin + blockIdx.x];
+    int tile, part, parts;
+    if (!lookup_item(a, tile, part, parts))
+        return;
+    const TileMeta m = a.meta[tile];
     const bool f16 = (m.flags & kTileF16) != 0;
 #define EDM_MK(KK)                                                                                                     \
     case KK:                                                                                                           \
         if (f16 && KK <= kF16MaxK)                                                                                     \
-            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true, EDM_RB, EDM_LAG>(a);                                     \
+            lookup_chunk_body<(KK <= kF16MaxK ? KK : 2), true, EDM_RB, EDM_LAG>(a, tile, part, parts);                  \
         else                                                                                                           \
-            lookup_chunk_body<KK, false, EDM_RB, EDM_LAG>(a);                                                          \
+            lookup_chunk_body<KK, false, EDM_RB, EDM_LAG>(a, tile, part, parts);                                       \
         break;
     switch (m.E + 1) {
         EDM_MK(2)
@@ -58,7 +61,7 @@ cudaError_t EDM_MULTI_LAUNCH(const LookupArgs &a, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(EDM_MULTI_NAME, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    dim3 grid((unsigned)a.n_tiles, (unsigned)a.lib_parts);
+    const dim3 grid = a.slot ? dim3((unsigned)a.n_tiles) : dim3((unsigned)a.n_tiles, (unsigned)a.lib_parts);
     EDM_MULTI_NAME<<<grid, kCkThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

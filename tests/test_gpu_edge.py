@@ -120,3 +120,47 @@ def test_random_parameters_against_oracle(edm):
             got = edm.edm_ccm_rho(Yd, Ed, tau=tau, Tp=Tp, exclusion_radius=excl, precision=prec)
             got = got.cpu().numpy()[:, rows].T
             assert np.abs(got - R).max() < tol, (case, prec, tau, Tp, excl, N, T)
+
+
+def test_unusable_optE_gives_nan_rows_or_invalid(edm):
+    """optE values outside 1..EDM_MAX_E: the device-planned call (no host
+    synchronisation) writes NaN for those targets and the oracle's values
+    for every other; with EDM_FLAG_VALIDATE optE is checked on the host and
+    the call returns EDM_ERR_INVALID."""
+    Y = synth.coupled_logistic(20, 300, 0.05, 0.05, seed_data=94, seed_noise=95)
+    E = np.random.default_rng(96).integers(1, 6, size=20).astype(np.int32)
+    R = orc.ccm_rho_rows(Y, E)
+    Eb = E.copy()
+    Eb[4], Eb[11] = 0, edm.EDM_MAX_E + 1
+    got = edm.edm_ccm_rho(_dev(Y), torch.from_numpy(Eb).cuda()).cpu().numpy()  # [target][library]
+    assert np.isnan(got[[4, 11]]).all()
+    keep = [j for j in range(20) if j not in (4, 11)]
+    assert np.abs(got[keep].T - R[:, keep]).max() < RHO_TOL
+    with pytest.raises(edm.EdmError) as ei:
+        edm.edm_ccm_rho(_dev(Y), torch.from_numpy(Eb).cuda(), flags=edm.EDM_FLAG_VALIDATE)
+    assert ei.value.status == 1
+
+
+def test_cross_map_needs_no_host_synchronisation(edm):
+    """The cross map plans its E grouping on the device, so a whole call can
+    be recorded into a CUDA graph (a synchronisation or a device-to-host read
+    would end the capture with an error) and replayed: the replay on new data
+    equals a direct call."""
+    Y1 = synth.coupled_logistic(300, 500, 0.05, 0.05, seed_data=97, seed_noise=98)
+    Y2 = synth.coupled_logistic(300, 500, 0.05, 0.05, seed_data=99, seed_noise=100)
+    Yd = _dev(Y1)
+    E = torch.from_numpy(np.random.default_rng(101).integers(1, 9, size=300).astype(np.int32)).cuda()
+    out = torch.empty((300, 300), dtype=torch.float32, device="cuda")
+    ws = torch.empty(edm.edm_ccm_workspace_bytes(300, 500), dtype=torch.uint8, device="cuda")
+    edm.edm_ccm_rho(Yd, E, out=out, workspace=ws)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            edm.edm_ccm_rho(Yd, E, out=out, workspace=ws)
+    Yd.copy_(_dev(Y2))
+    g.replay()
+    torch.cuda.synchronize()
+    ref = edm.edm_ccm_rho(_dev(Y2), E)
+    assert torch.equal(out, ref)

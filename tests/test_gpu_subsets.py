@@ -69,8 +69,15 @@ def test_skill_converges_with_library_size(edm):
 
 
 def test_subset_too_small_is_rejected(edm):
+    """A subset that leaves fewer than E+1 candidates: EDM_ERR_INVALID with
+    EDM_FLAG_VALIDATE (checked on the host), else a NaN plane (checked on the
+    device, no host synchronisation)."""
     Y = synth.coupled_logistic(4, 200, 0.08, 0.05, seed_data=85, seed_noise=86)
     masks = synth.library_subsets(200, 5, 198, sizes=(5,), samples=1, seed=11)
+    full = np.full((1, (200 + 31) // 32), 0xFFFFFFFF, np.uint32)
+    E = torch.full((4,), 6, dtype=torch.int32, device="cuda")
     with pytest.raises(edm.EdmError) as ei:
-        edm.edm_ccm_rho_subsets(_dev(Y), torch.full((4,), 6, dtype=torch.int32, device="cuda"), _masks_dev(masks))
+        edm.edm_ccm_rho_subsets(_dev(Y), E, _masks_dev(masks), flags=edm.EDM_FLAG_VALIDATE)
     assert ei.value.status == 1
+    G = edm.edm_ccm_rho_subsets(_dev(Y), E, _masks_dev(np.concatenate([masks, full]))).cpu().numpy()
+    assert np.isnan(G[0]).all() and np.isfinite(G[1]).all()
