@@ -529,11 +529,11 @@ bool host_plan_needed(int64_t T, const edm_params *p, int64_t s_lo)
 }
 
 // Plan on the device from device optE (no host synchronisation): fixed
-// groups -- one over every E when all tiles fit one target block, else one
-// per E up to knn_thread_max_E() and one for the larger E, cut into target
-// blocks for long series -- whose tile ranges the plan kernel writes into
-// launch slots; targets with an unusable E get NaN rows (nan_* spec).  Then
-// stage the target tiles.
+// groups -- one over every E when the tiles sit in shared memory or all fit
+// one target block, else (long series, tiles read from L2) one per E up to
+// knn_thread_max_E() and one for the larger E, cut into target blocks --
+// whose tile ranges the plan kernel writes into launch slots; targets with
+// an unusable E get NaN rows (nan_* spec).  Then stage the target tiles.
 int ccm_prepare_dev(const float *Y, int64_t N, int64_t T, int64_t ldY, const int32_t *optE_d, const edm_params *params,
                     void *ws, cudaStream_t st, CcmPlan &P, int s_lo, float *nan_rho, int64_t ld_rho, int64_t row_len,
                     int planes, int64_t plane_stride)
@@ -564,7 +564,7 @@ int ccm_prepare_dev(const float *Y, int64_t N, int64_t T, int64_t ldY, const int
         u = (int)((N + P.RB / 4 - 1) / (P.RB / 4)) + (ehi - elo + 1);
         return std::min(u, n_tiles_max);
     };
-    if (n_tiles_max <= tpb) {
+    if (n_tiles_max <= tpb || !P.l2) {
         P.groups.push_back(DevGroup{1, EDM_MAX_E, (1u << EDM_MAX_E) - 1u, 0, 1, n_tiles_max});
     } else {
         const int thr = edm::knn_thread_max_E();
@@ -663,13 +663,15 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
     // per register class
     const int want = (P.l2 ? 4 : 16) * sms;
     // --- target groups x library blocks ----------------------------------------
-    // One group per E up to knn_thread_max_E() (the tables of that E, one
-    // build per library), the larger E together (one warp-kernel sweep
-    // serves them all), so every (library, E) table is built once.  Tiles in
-    // shared memory: each library block's tables stay in L2 while the whole
-    // group's tiles stream through shared memory.  Tiles read from L2 (long
-    // series): a group is further cut into L2-sized target blocks, so its
-    // tiles stay resident while every library block sweeps them.
+    // Tiles in shared memory: one group over every E; a library block's
+    // tables (one warp-kernel sweep per library builds every E in use) are
+    // read by all tiles, which stream through shared memory, the largest E
+    // first; each warp prefetches its next library's table into L2.  Tiles
+    // read from L2 (long series): one group per E up to knn_thread_max_E()
+    // (the tables of that E, one build per library) and one for the larger
+    // E, each cut into L2-sized target blocks so its tiles stay resident
+    // while every library block sweeps them.  Either way every (library, E)
+    // table is built once per target block.
     struct LaunchGroup {
         uint32_t sel;                  // E set of the table layout
         int tb0, ntb;                  // host plan: tile range
@@ -689,11 +691,13 @@ int ccm_execute(const CcmPlan &P, const float *Y, int64_t N, int64_t T, int64_t 
         const size_t tile_bytes = (size_t)T * P.RB;
         const int tiles_per_block = (int)std::max<size_t>(1, kTileBlockBytes / tile_bytes);
         std::vector<std::pair<int, int>> ranges;  // tile ranges [first, last)
-        // all tiles within one target block: one group, so one warp-kernel
-        // sweep serves every E (no table is built twice either way; per-E
-        // thread launches measured slower there: 28.7 vs 26.5 ms per step at
-        // N = 1,000, T = 1,000)
-        if (n_tiles <= tiles_per_block)
+        // tiles in shared memory, or all tiles within one target block: one
+        // group, so one warp-kernel sweep per library builds the tables of
+        // every E in use (measured at N = 101,729, T = 1,500: kNN 4.45 s
+        // against 5.05 s for per-E groups with the thread kernel for E <= 6,
+        // lookup 11.24 against 11.41 s with the largest-E tiles scheduled
+        // first)
+        if (n_tiles <= tiles_per_block || !P.l2)
             ranges.emplace_back(0, n_tiles);
         for (int t0 = ranges.empty() ? 0 : n_tiles; t0 < n_tiles;) {
             const int E = tiles[(size_t)t0].E;

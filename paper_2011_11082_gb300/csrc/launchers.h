@@ -164,6 +164,9 @@ struct LookupArgs {
 };
 
 // (tile, library part) of this CTA, or false when the CTA has no work.
+// Tiles are sorted by ascending E and a tile's cost grows with E, so the
+// blocks take them from the last one backwards: the costliest tiles start
+// in the first wave and the cheap ones fill the tail.
 __device__ __forceinline__ bool lookup_item(const LookupArgs &a, int &tile, int &part, int &parts)
 {
     if (a.slot) {
@@ -175,11 +178,11 @@ __device__ __forceinline__ bool lookup_item(const LookupArgs &a, int &tile, int 
         parts = parts < 1 ? 1 : (parts > cap ? cap : parts);
         if ((int)blockIdx.x >= ntb * parts)
             return false;
-        tile = a.slot->tile_begin + (int)blockIdx.x / parts;
+        tile = a.slot->tile_begin + ntb - 1 - (int)blockIdx.x / parts;
         part = (int)blockIdx.x % parts;
         return true;
     }
-    tile = a.tile_begin + (int)blockIdx.x;
+    tile = a.tile_begin + a.n_tiles - 1 - (int)blockIdx.x;
     part = (int)blockIdx.y;
     parts = a.lib_parts;
     return true;

@@ -468,10 +468,20 @@ __device__ __forceinline__ void lookup_chunk_body(const LookupArgs &a, int tile,
     const int lib_hi = min(a.n_lib, lib_lo + per);
     cx.lane16 = (uint32_t)lane_sub<RB>(lane) * 16u;
 
+    // table bytes of one (library, E): K weight rows and K index rows of
+    // Tq_pad entries (both 16-byte multiples at 16-byte aligned offsets)
+    const uint32_t w_bytes = (uint32_t)(K * a.lay.Tq_pad * 4), i_bytes = (uint32_t)(K * a.lay.Tq_pad * 2);
     for (int lib = lib_lo + warp; lib < lib_hi; lib += kCkWarps) {
         const uint8_t *lb = a.tables + (size_t)lib * a.lay.lib_stride;
         const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
         const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        // the warp's next library: its table into L2 while this one runs
+        // (tables of a large library block live in HBM)
+        if (lane == 0 && lib + kCkWarps < lib_hi) {
+            const uint8_t *nb = lb + (size_t)kCkWarps * a.lay.lib_stride;
+            bulk_prefetch_l2(nb + a.lay.off_w[E], w_bytes);
+            bulk_prefetch_l2(nb + a.lay.off_i[E], i_bytes);
+        }
         float tot[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
         for (int pass = 0; pass < PASSES; ++pass) {
