@@ -311,6 +311,25 @@ def bench_batched(args, lib, edm, _abi, torch, edm_synth):
                "h2d_bytes_per_step": int(sum(Y.nbytes for Y in data)),
                "d2h_bytes_per_step": int(sum(Y.shape[0] ** 2 * 4 + Y.shape[0] * 4 for Y in data)),
                "host_buffers": "pinned", "api": "CCMBatch.run (edm_ccm_rho_batched)"}
+    # the adjoint of the global mean rho (indices and optE frozen) for every
+    # dataset, timed the same way (per-dataset edm_ccm_rho_backward calls)
+    backward = None
+    if not args.no_backward:
+        grads = batch.mean_rho_grad()  # warm-up (workspaces)
+        torch.cuda.synchronize()
+        bl0 = [lib.edm_launch_count(k) for k in range(_abi.EDM_KERNEL_BATCH)]
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            grads = batch.mean_rho_grad()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / args.steps
+        backward = {"ms_per_step": bms, "what": "dL/dY of the global mean rho over all 256 datasets "
+                    "(edm_ccm_rho_backward per dataset: kNN tables rebuilt, target and library passes)",
+                    "gpu_launches": sum(lib.edm_launch_count(k) - bl0[k] for k in range(_abi.EDM_KERNEL_BATCH)),
+                    "grad_values": int(sum(g.numel() for g in grads))}
     line = {"metric": "cross-map pairs/s, batched form (256 datasets, 1 GB300)", "value": pairs / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -318,7 +337,8 @@ def bench_batched(args, lib, edm, _abi, torch, edm_synth):
             "config": {"workload": BATCHED, "datasets": len(data), "pairs": pairs, "E_max": 20,
                        "precision": args.precision, "graph": "one cudaGraphLaunch per step",
                        "l2": "series 0.9 GB in total, rho 0.39 GB (rho alone exceeds L2)"},
-            "roofline": roofline, "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": launches}
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "backward": backward}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -408,6 +428,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-target sub-record of an FP32 run")
+    ap.add_argument("--no-backward", action="store_true", help="batched workload: skip timing the adjoint")
     ap.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
                     help="dataset-size sweep (one JSON line per size) instead of the benchmark line")
     ap.add_argument("--size", default=None, help="with --sweep: one size NxT instead of the sweep's list")

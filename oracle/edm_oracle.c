@@ -645,6 +645,42 @@ int orc_ccm_rho_pairs(const double *Y, int64_t N, int64_t T, int64_t ldY, const 
     return rc_all;
 }
 
+/*
+ * Phase-2 tables (as orc_ccm_table) of library rows rows[0..n_rows) of Y at
+ * one E, one library per thread: idx[r][nq][E+1] and, if w is not NULL,
+ * w[r][nq][E+1] (nq = orc_ccm_rows).  A convenience for checks that need
+ * many libraries' frozen neighbour indices; the per-library arithmetic is
+ * orc_ccm_table's.
+ */
+int orc_ccm_tables(const double *Y, int64_t ldY, int64_t T, const int64_t *rows, int64_t n_rows, int E, int tau,
+                   int Tp, int excl, int64_t *idx, double *w, int nthreads)
+{
+    const int64_t nq = orc_ccm_rows(T, E, tau, Tp);
+    const int k = E + 1;
+    if (nq < 1)
+        return ORC_ERR_INVALID;
+    int rc_all = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads < 1)
+        nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int64_t r = 0; r < n_rows; ++r) {
+        double *wr = w ? w + r * nq * k : (double *)malloc(sizeof(double) * (size_t)(nq * k));
+        int rc = wr ? orc_ccm_table(Y + rows[r] * ldY, T, E, tau, Tp, excl, idx + r * nq * k, wr) : ORC_ERR_NOMEM;
+        if (!w)
+            free(wr);
+        if (rc != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            rc_all = rc;
+        }
+    }
+    (void)nthreads;
+    return rc_all;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -81,6 +81,8 @@ def _declare(lib):
     lib.orc_ccm_rho_subsets.restype = _int
     lib.orc_ccm_rho_subsets.argtypes = [_dp, _i64, _i64, _i64, _i32p, _i64p, _i64, ctypes.POINTER(ctypes.c_uint32), _i64,
                                         _i64, _int, _int, _int, _dp, _int]
+    lib.orc_ccm_tables.restype = _int
+    lib.orc_ccm_tables.argtypes = [_dp, _i64, _i64, _i64p, _i64, _int, _int, _int, _int, _i64p, _dp, _int]
     lib.orc_max_threads.restype = _int
     lib.orc_max_threads.argtypes = []
     return lib
@@ -175,6 +177,22 @@ def ccm_table(x, E, tau=1, Tp=1, excl=0, lib=None):
     if rc:
         raise ValueError(f"orc_ccm_table failed ({rc})")
     return idx, w
+
+
+def ccm_tables(Y, E, rows=None, tau=1, Tp=1, excl=0, nthreads=None, lib=None):
+    """Neighbour indices of the phase-2 tables of library rows `rows` of Y at
+    one E (as ccm_table, libraries spread over threads): int64
+    [len(rows)][nq][E+1]."""
+    Y = _f64(np.atleast_2d(Y))
+    N, T = Y.shape
+    rows = np.arange(N, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nq = ccm_rows(T, E, tau, Tp, lib=lib)
+    idx = np.zeros((rows.size, nq, E + 1), np.int64)
+    rc = (lib or _load()).orc_ccm_tables(_ptr(Y, _dp), T, T, _ptr(rows, _i64p), rows.size, E, tau, Tp, excl,
+                                         _ptr(idx, _i64p), None, nthreads or default_threads())
+    if rc:
+        raise ValueError(f"orc_ccm_tables failed ({rc})")
+    return idx
 
 
 def ccm_table_d2(x, E, idx, tau=1, Tp=1, lib=None):

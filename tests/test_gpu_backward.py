@@ -37,7 +37,7 @@ def test_backward_matches_fp64_reference_gradient(edm):
     assert abs(L.item() - L_ref) < 1e-5
     G = Yd.grad.cpu().numpy()
     scale = np.abs(G_ref).max()
-    assert np.abs(G - G_ref).max() < 2e-3 * scale, (np.abs(G - G_ref).max(), scale)
+    assert np.abs(G - G_ref).max() < 1e-4 * scale + 1e-7, (np.abs(G - G_ref).max(), scale)
 
 
 def test_backward_general_upstream_gradient(edm):
@@ -56,7 +56,7 @@ def test_backward_general_upstream_gradient(edm):
     G_ref = Yt.grad.numpy()
     g_t = torch.from_numpy(C.T.astype(np.float32)).contiguous().cuda()  # target-major
     G = edm.edm_ccm_rho_backward(torch.from_numpy(Y).cuda(), torch.from_numpy(optE).cuda(), g_t).cpu().numpy()
-    assert np.abs(G - G_ref).max() < 2e-3 * np.abs(G_ref).max()
+    assert np.abs(G - G_ref).max() < 1e-4 * np.abs(G_ref).max() + 1e-7, (np.abs(G - G_ref).max(), np.abs(G_ref).max())
 
 
 def test_backward_finite_differences_batched_style(edm):
