@@ -412,6 +412,86 @@ def bench_sweep(args, lib, edm, _abi, torch, edm_synth):
     return 0
 
 
+def bench_self_scheduled(args, lib, edm, _abi, torch, edm_synth, dist, world, rank, local):
+    """One problem over all ranks (strong scaling): the paper's self-scheduled
+    decomposition (Sec. III-C) with the CUDA entry points -- every rank takes
+    the next block of series (phase 1), then, after every block's optE is in
+    the store (the paper's broadcast), the next block of library rows
+    (phase 2), writing its own columns of a target-major rho; no data-path
+    collective.  A step is one full run; `value` = N^2 / (max over ranks of
+    the step time)."""
+    from paper_2011_11082_gb300.sharding import run_self_scheduled
+
+    dev = torch.device("cuda", local)
+    N, T, dens, bmax, E_max = WORKLOADS[args.workload]
+    Y = edm_synth.coupled_logistic(N, T, dens, bmax, seed_data=0, seed_noise=1)  # the same problem on every rank
+    Yd = torch.from_numpy(Y).to(dev)
+    rho = torch.empty((N, N), dtype=torch.float32, device=dev)
+    ws = torch.empty(edm.edm_ccm_workspace_bytes(N, T), dtype=torch.uint8, device=dev)
+    store = dist.distributed_c10d._get_default_store() if dist else None
+    if store is None:
+        import torch.distributed as tdist
+
+        store = tdist.HashStore()  # one rank: a local store
+    stream = torch.cuda.current_stream(dev)
+
+    def opt(Yb):
+        e, _ = edm.edm_optimal_E(Yb, E_max=E_max, return_rho=False)
+        return e.cpu().numpy()
+
+    def rows(Yf, optE, lo, hi):
+        edm.edm_ccm_rho(Yd, optE.to(dev), lib_begin=lo, lib_count=hi - lo, out=rho[:, lo:hi], workspace=ws)
+        return hi - lo
+
+    def step(k):
+        _, mine = run_self_scheduled(Yd, opt, rows, store, block=args.lib_block, phase1_block=args.series_block,
+                                     tag=f"bench/{k}")
+        return mine
+
+    k = 0
+    for _ in range(args.warmup):
+        step(k)
+        k += 1
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    blocks = 0
+    for _ in range(args.steps):
+        blocks += len(step(k))
+        k += 1
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": float(N) * N / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "N": N, "T": T, "E_max": E_max, "tau": 1, "Tp": 1,
+                           "partition": "self-scheduled blocks: phase 1 by series, optE through the store, "
+                                        "phase 2 by library rows",
+                           "series_block": args.series_block, "lib_block": args.lib_block,
+                           "l2": "inputs larger than L2 (series 0.6 GB, rho 41 GB)"},
+                "blocks_rank0": blocks, "e2e": None, "cpu_baseline": None, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,6 +509,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-target sub-record of an FP32 run")
     ap.add_argument("--no-backward", action="store_true", help="batched workload: skip timing the adjoint")
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "self"],
+                    help="N > 1: independent problems per rank (replicas, weak scaling) or one problem "
+                         "self-scheduled over the ranks in blocks (self, strong scaling)")
+    ap.add_argument("--series-block", type=int, default=8192, help="--partition self: series per phase-1 block")
+    ap.add_argument("--lib-block", type=int, default=4096, help="--partition self: library rows per phase-2 block")
     ap.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
                     help="dataset-size sweep (one JSON line per size) instead of the benchmark line")
     ap.add_argument("--size", default=None, help="with --sweep: one size NxT instead of the sweep's list")
@@ -457,6 +542,8 @@ def main():
     lib = _abi.load()
     if args.workload == BATCHED:
         return bench_batched(args, lib, edm, _abi, torch, edm_synth)
+    if args.partition == "self":
+        return bench_self_scheduled(args, lib, edm, _abi, torch, edm_synth, dist, world, rank, local)
     if args.sweep:
         return bench_sweep(args, lib, edm, _abi, torch, edm_synth)
 

@@ -125,3 +125,54 @@ def test_self_scheduled_ranks_cover_every_block_once(tmp_path):
     assert np.array_equal(got, R)
     counts = [sum(1 for v in owners.values() if v == r) for r in range(3)]
     assert counts[0] <= max(counts[1], counts[2]), counts
+
+
+def _steps_worker(rank, world, port, Y, E_max, out_dir):
+    """The strong-scaling bench mode's use of the runtime: the default store of
+    a gloo process group, one tag per step, several steps in a row."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import oracle as orc
+    from paper_2011_11082_gb300.sharding import run_self_scheduled
+
+    store = dist.distributed_c10d._get_default_store()
+    N = Y.shape[0]
+    for k in range(2):
+        rho = np.full((N, N), np.nan)  # this rank's columns of a target-major map
+
+        def opt(Ys):
+            return orc.optimal_E(Ys, E_max, nthreads=1)[0]
+
+        def rows(Yf, optE, b, e):
+            rho[:, b:e] = orc.ccm_rho_rows(Yf, optE.numpy(), rows=np.arange(b, e), nthreads=1).T
+            return e - b
+
+        optE, blocks = run_self_scheduled(Y, opt, rows, store, block=3, phase1_block=4, tag=f"bench/{k}")
+        np.save(os.path.join(out_dir, f"st{k}_rho_{rank}.npy"), rho)
+        np.save(os.path.join(out_dir, f"st{k}_optE_{rank}.npy"), optE.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_self_scheduled_steps_on_the_process_group_store(tmp_path):
+    """Two ranks, two consecutive steps on the process group's own store:
+    in each step the ranks' columns together form the single-process
+    target-major map, every column exactly once."""
+    from oracle import oracle as orc
+
+    Y = synth.coupled_logistic(11, 140, 0.1, 0.05, seed_data=25, seed_noise=26)
+    E_max = 4
+    port = _free_port()
+    mp.start_processes(_steps_worker, args=(2, port, Y, E_max, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    oE, _ = orc.optimal_E(Y, E_max)
+    R = orc.ccm_rho_rows(Y, oE).T  # target-major
+    for k in range(2):
+        parts = [np.load(tmp_path / f"st{k}_rho_{r}.npy") for r in range(2)]
+        have = [~np.isnan(p).all(axis=0) for p in parts]
+        assert not np.any(have[0] & have[1]) and np.all(have[0] | have[1])
+        got = np.where(have[0][None, :], parts[0], parts[1])
+        assert np.array_equal(got, R)
+        for r in range(2):
+            assert np.array_equal(np.load(tmp_path / f"st{k}_optE_{r}.npy"), oE)
