@@ -33,21 +33,23 @@ def test_smem_gather_bytes_counts_gathers_and_observation():
 
 def test_traffic_record_matches_sources_or_is_dropped(tmp_path, monkeypatch):
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "lookup_dram_traffic.json")))
-    e = rec["n101729_t1500/fp32"]
+    e = rec["n16384_t1500/fp32"]
     assert e["bytes_per_pair"] > 4.0  # at least the rho write
     assert abs(e["bytes_per_pair"] * e["pairs_per_captured_launch"] - e["bytes_per_captured_launch"]) < 1.0
     # a stale record (other sources) gives no traffic figure
     stale = dict(rec)
-    stale["n101729_t1500/fp32"] = dict(e, sources="0" * 16)
+    stale["n16384_t1500/fp32"] = dict(e, sources="0" * 16)
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "lookup_dram_traffic.json").write_text(json.dumps(stale))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "_lookup_sources_hash", lambda: "1" * 16)
-    assert bench._measured_traffic("n101729_t1500", "fp32", 1e6) is None
+    assert bench._measured_traffic("n16384_t1500", "fp32", 1e6) is None
     # a current record scales with the pairs of the launch
     monkeypatch.setattr(bench, "_lookup_sources_hash", lambda: "0" * 16)
-    assert bench._measured_traffic("n101729_t1500", "fp32", 2e6) == e["bytes_per_pair"] * 2e6
-    assert bench._measured_traffic("n101729_t1500", "fp16", 2e6) is None
+    assert bench._measured_traffic("n16384_t1500", "fp32", 2e6) == e["bytes_per_pair"] * 2e6
+    assert bench._measured_traffic("n16384_t1500", "fp16", 2e6) is None
+    # no record for the full-size workload (its traffic is not scaled from the small case)
+    assert bench._measured_traffic("n101729_t1500", "fp32", 2e6) is None
 
 
 def test_sweep_sizes():
