@@ -19,6 +19,8 @@
 // Pass 1 (one CTA per target) also stores (alpha, beta, p_bar) per pair for
 // pass 2 (one CTA per library).  Both accumulate in shared memory with
 // atomic adds and then add their row of grad_Y once.
+#include <algorithm>
+
 #include "edm_internal.cuh"
 #include "launchers.h"
 
@@ -152,14 +154,17 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
         dst[t] += gy[t];
 }
 
-// Pass 2: one CTA per library in the block.  H is [k][rows of the chunk].
-__global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_rows)
+// Pass 2: one CTA per library in the block.  For each E, in chunks of
+// rows: the chunk's table entries (W and I) are staged in shared memory
+// once, then every target of that E adds its terms to H [k][rows of the
+// chunk] from shared memory only.
+__global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int buf_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float *x = reinterpret_cast<float *>(smem);
     float *gx = x + a.T;
     float *yb = gx + a.T;
-    float *H = yb + a.T;
+    unsigned char *buf = reinterpret_cast<unsigned char *>(yb + a.T);
     const int li = blockIdx.x;
     const int64_t i = a.lib0 + li;
     const float *src = a.Y + i * a.ldY;
@@ -179,10 +184,20 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_
         const int Tq = a.T - a.Tp - L;
         const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
         const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        // rows per chunk: H and W (4 bytes each) and I (2 bytes) per entry,
+        // a multiple of 4 rows so the arrays stay 16-byte aligned
+        const int h_rows = max(4, min((Tq + 3) & ~3, (buf_bytes / (10 * k)) & ~3));
         for (int r0 = 0; r0 < Tq; r0 += h_rows) {
             const int rn = min(h_rows, Tq - r0);
-            for (int q = threadIdx.x; q < k * rn; q += blockDim.x)
-                H[q] = 0.f;
+            float *H = reinterpret_cast<float *>(buf);
+            float *Ws = H + (size_t)k * h_rows;
+            uint16_t *Is = reinterpret_cast<uint16_t *>(Ws + (size_t)k * h_rows);
+            for (int q = threadIdx.x; q < k * rn; q += blockDim.x) {
+                const int nn = q / rn, rr = q - nn * rn;
+                H[nn * h_rows + rr] = 0.f;
+                Ws[nn * h_rows + rr] = Wt[nn * tq + r0 + rr];
+                Is[nn * h_rows + rr] = It[nn * tq + r0 + rr];
+            }
             __syncthreads();
             for (int pj = j0; pj < j1; ++pj) {
                 const int j = a.pi[pj];
@@ -196,10 +211,10 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_
                     const int r = r0 + rr;
                     float pv = 0.f;
                     for (int nn = 0; nn < k; ++nn)
-                        pv = fmaf(Wt[nn * tq + r], yb[It[nn * tq + r]], pv);
+                        pv = fmaf(Ws[nn * h_rows + rr], yb[Is[nn * h_rows + rr]], pv);
                     const float at = st.x * (yb[L + r + a.Tp] - ob) - st.y * (pv - st.z);
                     for (int nn = 0; nn < k; ++nn)
-                        H[nn * rn + rr] += at * (yb[It[nn * tq + r]] - pv);
+                        H[nn * h_rows + rr] += at * (yb[Is[nn * h_rows + rr]] - pv);
                 }
                 __syncthreads();
             }
@@ -209,7 +224,7 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_
                 const int t = L + r;
                 float d[EDM_MAX_E + 1];
                 for (int nn = 0; nn < k; ++nn) {
-                    const int s = (int)It[nn * tq + r] - a.Tp;
+                    const int s = (int)Is[nn * h_rows + rr] - a.Tp;
                     float acc = 0.f;
                     for (int m = 0; m < E; ++m) {
                         float df = x[t - m * a.tau] - x[s - m * a.tau];
@@ -222,12 +237,12 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_
                     continue;  // duplicate-only weights: constant
                 float g0 = 0.f;
                 for (int nn = 1; nn < k; ++nn) {
-                    const float wv = Wt[nn * tq + r];
-                    const float h = H[nn * rn + rr];
+                    const float wv = Ws[nn * h_rows + rr];
+                    const float h = H[nn * h_rows + rr];
                     g0 += wv * d[nn] / (d1 * d1) * h;
                     const float gn = -(wv / d1) * h;
                     if (d[nn] > 0.f) {
-                        const int s = (int)It[nn * tq + r] - a.Tp;
+                        const int s = (int)Is[nn * h_rows + rr] - a.Tp;
                         const float cf = gn / d[nn];
                         for (int m = 0; m < E; ++m) {
                             float df = x[t - m * a.tau] - x[s - m * a.tau];
@@ -237,7 +252,7 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_
                     }
                 }
                 {
-                    const int s = (int)It[r] - a.Tp;
+                    const int s = (int)Is[rr] - a.Tp;
                     const float cf = g0 / d1;
                     for (int m = 0; m < E; ++m) {
                         float df = x[t - m * a.tau] - x[s - m * a.tau];
@@ -256,7 +271,10 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int h_
 
 int bw_max_T() { return kBwMaxRows * kBwThreads; }
 
-static size_t bw_lib_smem(int T, int h_rows, int kmax) { return (size_t)3 * T * 4 + (size_t)h_rows * kmax * 4; }
+// Library pass: x, gx and one target series (3T floats) and a buffer for a
+// chunk's H, W and I (10 bytes per row and neighbour), sized for about
+// 110 KB per CTA (two CTAs per SM) and at least 4 rows of the largest K.
+static size_t bw_lib_smem(int T, size_t buf_bytes) { return (size_t)3 * T * 4 + buf_bytes; }
 
 cudaError_t launch_backward(const BwArgs &a, int kmax, cudaStream_t st)
 {
@@ -267,18 +285,19 @@ cudaError_t launch_backward(const BwArgs &a, int kmax, cudaStream_t st)
     bw_target_kernel<<<a.N, kBwThreads, s1, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    // H chunk: as many rows as fit next to x, gx and the target buffer
-    const size_t budget = 200 * 1024 - (size_t)3 * a.T * 4;
-    int h_rows = (int)(budget / ((size_t)kmax * 4));
-    if (h_rows > a.T)
-        h_rows = a.T;
-    if (h_rows < 32)
+    const size_t fixed = (size_t)3 * a.T * 4;
+    const size_t target = 110 * 1024;
+    const size_t floor_bytes = (size_t)10 * kmax * 8;
+    size_t buf = target > fixed + floor_bytes ? target - fixed : floor_bytes;
+    buf = std::min(buf, (size_t)10 * kmax * (size_t)(a.T + 3));
+    buf &= ~(size_t)15;
+    const size_t s2 = bw_lib_smem(a.T, buf);
+    if (s2 > 227 * 1024)
         return cudaErrorInvalidValue;
-    size_t s2 = bw_lib_smem(a.T, h_rows, kmax);
     if ((e = cudaFuncSetAttribute(bw_library_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) !=
         cudaSuccess)
         return e;
-    bw_library_kernel<<<a.n_lib, kBwThreads, s2, st>>>(a, h_rows);
+    bw_library_kernel<<<a.n_lib, kBwThreads, s2, st>>>(a, (int)buf);
     return cudaGetLastError();
 }
 
