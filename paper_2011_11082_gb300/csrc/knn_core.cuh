@@ -41,8 +41,7 @@ __host__ __device__ constexpr int list_off(int E) { return (E - 1) * E / 2 + (E 
 constexpr int kListTotal = list_off(EDM_MAX_E + 1);
 
 struct __align__(16) KnnWarpScratch {
-    float cd[kCandCap];
-    int cs[kCandCap];
+    unsigned long long ck[kCandCap];  // buffered candidates as dkey(d2, s)
     float ld[kListTotal];
     int ls[kListTotal];
     double l64[kKmax];
@@ -134,55 +133,40 @@ __device__ __forceinline__ float kth_lane_min(float mn, int K)
     return __shfl_sync(kFull, srt, K - 1);
 }
 
-// Rank-select: the buffer holds c (<= kCandCap) entries; write the cap
-// smallest by (d, s) in order into the list at lo.  Returns the count kept.
+// Rank-select: the buffer holds c (<= kCandCap) keys; write the cap
+// smallest in order into the list at lo.  Returns the count kept.  Each lane
+// ranks its own one or two keys against all c, reading the buffer two keys
+// (16 bytes, a broadcast) at a time.
 __device__ __forceinline__ int buffer_to_list(KnnWarpScratch &sc, int c, int cap, int lo)
 {
     const int lane = lane_id();
-    if (c <= 32) {
-        float d0 = lane < c ? sc.cd[lane] : CUDART_INF_F;
-        int s0 = lane < c ? sc.cs[lane] : 0x7fffffff;
-        int r0 = 0;
-        for (int f = 0; f < c; ++f) {
-            float df = __shfl_sync(kFull, d0, f);
-            int sf = __shfl_sync(kFull, s0, f);
-            r0 += (df < d0) || (df == d0 && sf < s0);
-        }
-        __syncwarp();
-        if (lane < c && r0 < cap) {
-            sc.ld[lo + r0] = d0;
-            sc.ls[lo + r0] = s0;
-        }
-        __syncwarp();
-        return c < cap ? c : cap;
-    }
-    unsigned long long k0 = ~0ull, k1 = ~0ull;
-    float d0 = 0.f, d1 = 0.f;
-    int s0 = 0, s1 = 0;
-    if (lane < c) {
-        d0 = sc.cd[lane];
-        s0 = sc.cs[lane];
-        k0 = dkey(d0, s0);
-    }
-    if (lane + 32 < c) {
-        d1 = sc.cd[lane + 32];
-        s1 = sc.cs[lane + 32];
-        k1 = dkey(d1, s1);
-    }
+    if ((c & 1) && lane == 0)
+        sc.ck[c] = ~0ull;  // pad to a pair: ranks below no key
+    __syncwarp();
+    const unsigned long long k0 = lane < c ? sc.ck[lane] : ~0ull;
+    const unsigned long long k1 = lane + 32 < c ? sc.ck[lane + 32] : ~0ull;
+    const ulonglong2 *kp = reinterpret_cast<const ulonglong2 *>(sc.ck);
     int r0 = 0, r1 = 0;
-    for (int f = 0; f < c; ++f) {
-        unsigned long long kf = dkey(sc.cd[f], sc.cs[f]);
-        r0 += kf < k0;
-        r1 += kf < k1;
+    if (c <= 32) {
+        for (int f = 0; f < c; f += 2) {
+            const ulonglong2 kk = kp[f >> 1];
+            r0 += (int)(kk.x < k0) + (int)(kk.y < k0);
+        }
+    } else {
+        for (int f = 0; f < c; f += 2) {
+            const ulonglong2 kk = kp[f >> 1];
+            r0 += (int)(kk.x < k0) + (int)(kk.y < k0);
+            r1 += (int)(kk.x < k1) + (int)(kk.y < k1);
+        }
     }
     __syncwarp();
     if (lane < c && r0 < cap) {
-        sc.ld[lo + r0] = d0;
-        sc.ls[lo + r0] = s0;
+        sc.ld[lo + r0] = __uint_as_float((unsigned)(k0 >> 32));
+        sc.ls[lo + r0] = (int)(unsigned)k0;
     }
     if (lane + 32 < c && r1 < cap) {
-        sc.ld[lo + r1] = d1;
-        sc.ls[lo + r1] = s1;
+        sc.ld[lo + r1] = __uint_as_float((unsigned)(k1 >> 32));
+        sc.ls[lo + r1] = (int)(unsigned)k1;
     }
     __syncwarp();
     return c < cap ? c : cap;
@@ -192,11 +176,11 @@ __device__ __forceinline__ int buffer_to_list(KnnWarpScratch &sc, int c, int cap
 __device__ __forceinline__ unsigned long long buffer_kth_key(KnnWarpScratch &sc, int c, int K)
 {
     const int lane = lane_id();
-    unsigned long long k0 = lane < c ? dkey(sc.cd[lane], sc.cs[lane]) : ~0ull;
-    unsigned long long k1 = lane + 32 < c ? dkey(sc.cd[lane + 32], sc.cs[lane + 32]) : ~0ull;
+    unsigned long long k0 = lane < c ? sc.ck[lane] : ~0ull;
+    unsigned long long k1 = lane + 32 < c ? sc.ck[lane + 32] : ~0ull;
     int r0 = 0, r1 = 0;
     for (int f = 0; f < c; ++f) {
-        unsigned long long kf = dkey(sc.cd[f], sc.cs[f]);
+        unsigned long long kf = sc.ck[f];
         r0 += kf < k0;
         r1 += kf < k1;
     }
@@ -283,20 +267,27 @@ __device__ __forceinline__ float stored_d2(const KnnQuery &q, int j)
 }
 
 // Write the marked candidates of this lane with key <= kth into the buffer
-// from position pos on (positions >= kCandCap are dropped).
+// from position pos on (positions >= kCandCap are dropped).  Two slots per
+// round, so their scratch loads are in flight together.
 __device__ __forceinline__ void store_marked(const KnnQuery &q, KnnWarpScratch &sc, unsigned m0, unsigned m1, int c0,
                                              int pos, unsigned long long kth)
 {
     const int lane = lane_id();
+    const int s_lane = q.s_first + c0 + lane;
     while (m0 | m1) {
-        const int j = pop_slot(m0, m1);
-        const int s = q.s_first + c0 + lane + 32 * j;
-        const float d = stored_d2(q, j);
-        if (dkey(d, s) <= kth) {
-            if (pos < kCandCap) {
-                sc.cd[pos] = d;
-                sc.cs[pos] = s;
-            }
+        const int ja = pop_slot(m0, m1);
+        const bool two = (m0 | m1) != 0u;
+        const int jb = two ? pop_slot(m0, m1) : ja;
+        const unsigned long long ka = dkey(stored_d2(q, ja), s_lane + 32 * ja);
+        const unsigned long long kb = dkey(stored_d2(q, jb), s_lane + 32 * jb);
+        if (ka <= kth) {
+            if (pos < kCandCap)
+                sc.ck[pos] = ka;
+            ++pos;
+        }
+        if (two && kb <= kth) {
+            if (pos < kCandCap)
+                sc.ck[pos] = kb;
             ++pos;
         }
     }
@@ -338,11 +329,8 @@ __device__ __noinline__ int select_overflow(const KnnQuery q, KnnWarpScratch &sc
         const float dl = keep_l ? sc.ld[lo + lane] : 0.f;
         const int sl = keep_l ? sc.ls[lo + lane] : 0;
         __syncwarp();
-        if (keep_l) {
-            const int p = __popc(bl & ((1u << lane) - 1u));
-            sc.cd[p] = dl;
-            sc.cs[p] = sl;
-        }
+        if (keep_l)
+            sc.ck[__popc(bl & ((1u << lane) - 1u))] = dkey(dl, sl);
         store_marked(q, sc, m0, m1, c0, nl + off, kth);
         __syncwarp();
         c = nl + total;
@@ -618,10 +606,8 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
     if (c <= kCandCap) {
         int total;
         const int off = warp_excl_scan(__popc(m0) + __popc(m1), total);
-        if (lane < have) {
-            sc.cd[lane] = sc.ld[lo_l + lane];
-            sc.cs[lane] = sc.ls[lo_l + lane];
-        }
+        if (lane < have)
+            sc.ck[lane] = dkey(sc.ld[lo_l + lane], sc.ls[lo_l + lane]);
         store_marked(q, sc, m0, m1, c0, have + off, ~0ull);
         __syncwarp();
     } else {
