@@ -619,6 +619,20 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
     __syncwarp();
 }
 
+// Two slots of one lag: d += (xq - v)^2 per slot with packed FP32 pairs;
+// (xq - v) is formed as fma(v, -1, xq) (one rounding, as the plain
+// subtraction), so the sums are bitwise those of the scalar form.
+__device__ __forceinline__ void dist_step2(float &d0, float &d1, float xq, float v0, float v1)
+{
+    asm("{\n\t.reg .b64 D, V, Q, M;\n\t"
+        "mov.b64 D, {%0, %1};\n\tmov.b64 V, {%2, %3};\n\t"
+        "mov.b64 Q, {%4, %4};\n\tmov.b64 M, {%5, %5};\n\t"
+        "fma.rn.f32x2 Q, V, M, Q;\n\tfma.rn.f32x2 D, Q, Q, D;\n\t"
+        "mov.b64 {%0, %1}, D;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(v0), "f"(v1), "f"(xq), "f"(-1.0f));
+}
+
 // Full query: sweep all candidate chunks, then emit every selected E.
 template <int J, class Emit>
 __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
@@ -644,10 +658,8 @@ __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
             // lags before the series start read the +inf padding
             const float *xcj = q.xc + (q.s_first + c0 + lane - off);
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                float diff = xqv - xcj[32 * j];
-                d2[j] = fmaf(diff, diff, d2[j]);
-            }
+            for (int j = 0; j < J; j += 2)
+                dist_step2(d2[j], d2[j + 1], xqv, xcj[32 * j], xcj[32 * j + 32]);
             if ((q.sel >> (E - 1)) & 1u) {
                 select_E<J>(q, sc, d2, c0, E, prevE);
                 prevE = E;
