@@ -538,14 +538,16 @@ __device__ __forceinline__ int count_le(const float (&d2)[J], float th)
 // across it).  1) A threshold that at least K = E+3 real candidates meet:
 // the grown previous list (or this E's list of earlier chunks) when that
 // alone marks at most a buffer's worth, else its minimum with the K-th
-// smallest lane minimum.  2) If more than the buffer holds are at or below it, tighten it
+// smallest lane minimum.  For K <= kLaneMinK (and no list of earlier chunks)
+// the lane-minimum bound is taken at once: there the grown list marks too
+// many candidates in most selections.  2) If more than the buffer holds are at or below it, tighten it
 // by counting rounds on the registers (the count of points within squared
 // radius th grows about linearly for points near a low-dimensional
 // attractor), keeping the count >= K.  3) Store
 // the distances to the warp scratch, compact the marked candidates behind
 // the list kept from earlier chunks (exclusive warp scan of per-lane
 // counts), and rank them into the list.
-template <int J>
+template <int J, int kLaneMinK>
 __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, const float (&d2)[J], int c0, int E,
                                          int prevE)
 {
@@ -555,6 +557,8 @@ __device__ __forceinline__ void select_E(const KnnQuery &q, KnnWarpScratch &sc, 
     const int have = sc.lcount[E];
     // never mark a +inf slot (not a candidate): thresholds are clamped
     float th = fminf(seed_threshold(q, sc, E, prevE), 3.40282347e38f);
+    if (K <= kLaneMinK && have < K)
+        th = fminf(th, fminf(kth_lane_min(lane_min_tree(d2), K), 3.40282347e38f));
     unsigned m0 = 0u, m1 = 0u;
     int c = kCandCap + 1;
     if (th < 3.40282347e38f) {  // a seed exists: often tight enough alone
@@ -661,7 +665,7 @@ __device__ void knn_query(const KnnQuery &q, KnnWarpScratch &sc, Emit &emit)
             for (int j = 0; j < J; j += 2)
                 dist_step2(d2[j], d2[j + 1], xqv, xcj[32 * j], xcj[32 * j + 32]);
             if ((q.sel >> (E - 1)) & 1u) {
-                select_E<J>(q, sc, d2, c0, E, prevE);
+                select_E<J, Emit::kLaneMinK>(q, sc, d2, c0, E, prevE);
                 prevE = E;
             }
         }

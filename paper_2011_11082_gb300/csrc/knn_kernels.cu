@@ -73,6 +73,7 @@ struct SimplexMoments {
 };
 
 struct SimplexEmit {
+    static constexpr int kLaneMinK = 0;  // the grown list seeds every selection (measured faster here)
     const float *lib;  // library half (shared)
     const float *tgt;  // target half (shared)
     int Tp;
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kKnnThreads, 2) simplex_kernel(const float *__
 // Phase 2 tables.
 // ---------------------------------------------------------------------------
 struct EmitInternal {
+    static constexpr int kLaneMinK = 12;  // lane-minimum bound first for K <= 12
     uint8_t *lib_base;
     const TableLayout *lay;
     int t, tau, Tp;
@@ -227,6 +229,7 @@ struct EmitInternal {
 };
 
 struct EmitPublic {
+    static constexpr int kLaneMinK = 12;
     int32_t *idx;
     float *w;
     int t, tau, k_fixed;
