@@ -1096,7 +1096,11 @@ int edm_ccm_host(const float *Y_host, int64_t N, int64_t T, const edm_params *pa
 // Adjoint
 // ---------------------------------------------------------------------------
 namespace {
-constexpr size_t kBwTableBytes = 256ull << 20;
+// Table budget of the adjoint: all libraries at once when they fit in 1 GB
+// (the library pass runs one CTA per library of a block, so larger blocks
+// fill the GPU and the kNN and target passes run fewer times), else blocks
+// of as many libraries as 1 GB holds.
+constexpr size_t kBwTableBytes = 1ull << 30;
 
 struct BwWs {
     size_t pi, e_start, counts, meta, obar, stats, tables, table_bytes, total;
@@ -1124,7 +1128,7 @@ BwWs bw_layout(int64_t N, int64_t T, const edm_params *p)
     off += align256((size_t)N * (size_t)N * 16);
     w.tables = off;
     edm::TableLayout all = make_layout((1u << EDM_MAX_E) - 1u, T, p);
-    w.table_bytes = std::max(kBwTableBytes, (size_t)all.lib_stride);
+    w.table_bytes = std::max(std::min(kBwTableBytes, (size_t)N * all.lib_stride), (size_t)all.lib_stride);
     off += align256(w.table_bytes);
     w.total = off;
     return w;
