@@ -18,7 +18,13 @@
 //
 // Pass 1 (one CTA per target) also stores (alpha, beta, p_bar) per pair for
 // pass 2 (one CTA per library).  Both accumulate in shared memory with
-// atomic adds and then add their row of grad_Y once.
+// atomic adds and then add their row of grad_Y once.  The per-pair sums
+// are FP32 within a thread and a warp and FP64 across the warps (FP64 is a
+// small fraction of the FP32 rate on this GPU), over predictions shifted by
+// row 0's prediction K (d = p - K; equal predictions give exact zeros, so a
+// constant prediction keeps its zero variance and zero gradient): sum d,
+// then the centred sums of (d - d_bar)^2 and (d - d_bar)(o - o_bar).  The
+// means, variances and coefficients are FP64.
 #include <algorithm>
 
 #include "edm_internal.cuh"
@@ -48,6 +54,27 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh)
     return sh[0];
 }
 
+// Block sum of per-thread FP32 partials: FP32 within each warp, FP64 across
+// the warps.
+__device__ __forceinline__ double block_sum_f(float v, double *sh)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0)
+        sh[w] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum_d(t);
+        if (threadIdx.x == 0)
+            sh[0] = t;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
 // Pass 1: one CTA per target j, libraries lib0 .. lib0+n_lib-1.
 __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
 {
@@ -55,6 +82,7 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
     float *y = reinterpret_cast<float *>(smem);
     float *gy = y + a.T;
     __shared__ double sh[32];
+    __shared__ float shK;
     const int j = blockIdx.x;
     const float *src = a.Y + (int64_t)j * a.ldY;
     for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
@@ -96,7 +124,6 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
         const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
         const size_t tq = (size_t)a.lay.Tq_pad;
         float p[kBwMaxRows];
-        double sp = 0.0;
 #pragma unroll
         for (int q = 0; q < kBwMaxRows; ++q) {
             const int r = threadIdx.x + q * kBwThreads;
@@ -106,23 +133,32 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
                 for (int nn = 0; nn < k; ++nn)
                     acc = fmaf(Wt[nn * tq + r], y[It[nn * tq + r]], acc);
                 p[q] = acc;
-                sp += (double)acc;
             }
         }
-        sp = block_sum_d(sp, sh);
-        const double pb = sp / n;
-        double vp = 0.0, c = 0.0;
+        if (threadIdx.x == 0)
+            shK = p[0];  // row 0 (Tq >= 1)
+        __syncthreads();
+        const float K0 = shK;
+        float sdf = 0.f;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q)
+            if (threadIdx.x + q * kBwThreads < Tq)
+                sdf += p[q] - K0;
+        const double db = block_sum_f(sdf, sh) / n;
+        const double pb = (double)K0 + db;
+        const float dbf = (float)db, obf = (float)ob;
+        float vpf = 0.f, cf = 0.f;
 #pragma unroll
         for (int q = 0; q < kBwMaxRows; ++q) {
             const int r = threadIdx.x + q * kBwThreads;
             if (r < Tq) {
-                const double dp = (double)p[q] - pb;
-                vp += dp * dp;
-                c += dp * ((double)y[L + r + a.Tp] - ob);
+                const float dp = (p[q] - K0) - dbf;
+                vpf = fmaf(dp, dp, vpf);
+                cf = fmaf(dp, y[L + r + a.Tp] - obf, cf);
             }
         }
-        vp = block_sum_d(vp, sh);
-        c = block_sum_d(c, sh);
+        const double vp = block_sum_f(vpf, sh);
+        const double c = block_sum_f(cf, sh);
         const double g = (double)a.grad_rho[(int64_t)j * a.ld_g + i];
         double alpha = 0.0, beta = 0.0, gam = 0.0;
         if (vp > 0.0 && vo > 0.0) {
