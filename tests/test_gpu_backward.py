@@ -105,3 +105,36 @@ def test_backward_finite_differences_batched_style(edm):
         err = abs(fd - G[a, t])
         worst = max(worst, err / (abs(fd) + 1e-4))
         assert err < 1e-4 + 2e-2 * abs(fd), (a, t, fd, G[a, t])
+
+
+def test_backward_degenerate_series(edm):
+    """A constant series (row 3) and a two-level step (row 5).  As a target,
+    the constant series has zero observation variance: rho is NaN for every
+    library, and those pairs add nothing to the gradient.  As a library, its
+    distances are all 0 (neighbours by the tie rule, duplicate-only weights):
+    predictions equal but for the rows next to the exclusion window (on the
+    step target they are all equal: NaN again), and no gradient flows through
+    its distances.  Against the FP64 reference of L = sum over the finite
+    pairs of C_ij rho_ij; the adjoint gets C everywhere and must add nothing
+    for the NaN pairs."""
+    T = 300
+    Y = synth.coupled_logistic(10, T, 0.05, 0.05, seed_data=81, seed_noise=82)
+    Y[3, :] = 0.7
+    Y[5, : T // 2] = -0.4
+    Y[5, T // 2:] = 1.3
+    optE = np.random.default_rng(83).integers(1, 6, size=10).astype(np.int32)
+    C = np.random.default_rng(84).standard_normal((10, 10))
+    tabs = _tables(Y, optE)
+    Yt = torch.tensor(Y.astype(np.float64), requires_grad=True)
+    tot = 0
+    for i in range(10):
+        for j in range(10):
+            r = adjoint.rho_frozen(Yt[i], Yt[j], int(optE[j]), torch.as_tensor(tabs[(i, int(optE[j]))]))
+            if torch.isfinite(r):  # NaN: a side of zero variance
+                tot = tot + C[i, j] * r
+    tot.backward()
+    G_ref = Yt.grad.numpy()
+    g_t = torch.from_numpy(C.T.astype(np.float32)).contiguous().cuda()  # target-major, C everywhere
+    G = edm.edm_ccm_rho_backward(torch.from_numpy(Y).cuda(), torch.from_numpy(optE).cuda(), g_t).cpu().numpy()
+    assert np.isfinite(G).all()
+    assert np.abs(G - G_ref).max() < 1e-4 * np.abs(G_ref).max() + 1e-7, (np.abs(G - G_ref).max(), np.abs(G_ref).max())
