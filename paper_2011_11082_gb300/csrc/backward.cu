@@ -54,25 +54,117 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh)
     return sh[0];
 }
 
-// Block sum of per-thread FP32 partials: FP32 within each warp, FP64 across
-// the warps.
-__device__ __forceinline__ double block_sum_f(float v, double *sh)
+// Block sum of per-thread FP32 partials (two at once): FP32 within each
+// warp, FP64 across the warps.  Thread 0 receives the sums; the others 0.
+__device__ __forceinline__ void block_sum2_f(float v0, float v1, double *sh, double &s0, double &s1)
 {
-    v = warp_sum(v);
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0)
-        sh[w] = (double)v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-        t = warp_sum_d(t);
-        if (threadIdx.x == 0)
-            sh[0] = t;
+    if (l == 0) {
+        sh[2 * w] = (double)v0;
+        sh[2 * w + 1] = (double)v1;
     }
     __syncthreads();
-    return sh[0];
+    s0 = s1 = 0.0;
+    if (threadIdx.x < 32) {
+        const bool in = threadIdx.x < (int)(blockDim.x >> 5);
+        s0 = warp_sum_d(in ? sh[2 * threadIdx.x] : 0.0);
+        s1 = warp_sum_d(in ? sh[2 * threadIdx.x + 1] : 0.0);
+    }
+}
+
+// Per-pair scalars of pass 1, formed once by thread 0 and shared.
+struct BwPairScalars {
+    float dbf, fa, fb, fg, fpb;
+};
+
+// Pass 1 for one target of k neighbours: every library of the block in turn.
+__device__ __forceinline__ void bw_target_libs(const BwArgs &a, const float *y, float *gy, int j, int E, int k, int L,
+                                               int Tq, double ob, double vo, double *sh, BwPairScalars &ps)
+{
+    const double n = (double)Tq;
+    const double inv_n = 1.0 / n;
+    const float obf = (float)ob;
+    const size_t tq = (size_t)a.lay.Tq_pad;
+    for (int li = 0; li < a.n_lib; ++li) {
+        const int64_t i = a.lib0 + li;
+        const uint8_t *lb = a.tables + (size_t)li * a.lay.lib_stride;
+        const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
+        const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
+        float p[kBwMaxRows];
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q) {
+            const int r = threadIdx.x + q * kBwThreads;
+            p[q] = 0.f;
+            if (r < Tq) {
+                float acc = 0.f;
+                for (int nn = 0; nn < k; ++nn)
+                    acc = fmaf(__ldg(Wt + nn * tq + r), y[__ldg(It + nn * tq + r)], acc);
+                p[q] = acc;
+            }
+        }
+        // shift: row 0's prediction (Tq >= 1)
+        if (threadIdx.x == 0)
+            ps.fpb = p[0];
+        __syncthreads();
+        const float K0 = ps.fpb;
+        float sdf = 0.f;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q)
+            if (threadIdx.x + q * kBwThreads < Tq)
+                sdf += p[q] - K0;
+        double S, unused;
+        block_sum2_f(sdf, 0.f, sh, S, unused);
+        if (threadIdx.x == 0)
+            ps.dbf = (float)(S * inv_n);
+        __syncthreads();
+        const float dbf = ps.dbf;
+        float vpf = 0.f, cf = 0.f;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q) {
+            const int r = threadIdx.x + q * kBwThreads;
+            if (r < Tq) {
+                const float dp = (p[q] - K0) - dbf;
+                vpf = fmaf(dp, dp, vpf);
+                cf = fmaf(dp, y[L + r + a.Tp] - obf, cf);
+            }
+        }
+        double vp, c;
+        block_sum2_f(vpf, cf, sh, vp, c);
+        if (threadIdx.x == 0) {
+            const double pb = (double)K0 + S * inv_n;
+            const double g = (double)a.grad_rho[(int64_t)j * a.ld_g + i];
+            double alpha = 0.0, beta = 0.0, gam = 0.0;
+            if (vp > 0.0 && vo > 0.0) {
+                const double sq = sqrt(vp * vo);
+                const double rho = c / sq;
+                alpha = g / sq;
+                beta = g * rho / vp;
+                gam = g * rho / vo;
+            }
+            a.stats[i * a.N + j] = make_float4((float)alpha, (float)beta, (float)pb, 0.f);
+            ps.fa = (float)alpha;
+            ps.fb = (float)beta;
+            ps.fg = (float)gam;
+            ps.fpb = (float)pb;
+        }
+        __syncthreads();
+        const float fa = ps.fa, fb = ps.fb, fg = ps.fg, fpb = ps.fpb;
+#pragma unroll
+        for (int q = 0; q < kBwMaxRows; ++q) {
+            const int r = threadIdx.x + q * kBwThreads;
+            if (r < Tq) {
+                const float ov = y[L + r + a.Tp] - obf, pv = p[q] - fpb;
+                const float at = fa * ov - fb * pv;
+                const float bt = fa * pv - fg * ov;
+                for (int nn = 0; nn < k; ++nn)
+                    atomicAdd(&gy[__ldg(It + nn * tq + r)], at * __ldg(Wt + nn * tq + r));
+                atomicAdd(&gy[L + r + a.Tp], bt);
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // Pass 1: one CTA per target j, libraries lib0 .. lib0+n_lib-1.
@@ -82,7 +174,7 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
     float *y = reinterpret_cast<float *>(smem);
     float *gy = y + a.T;
     __shared__ double sh[32];
-    __shared__ float shK;
+    __shared__ BwPairScalars ps;
     const int j = blockIdx.x;
     const float *src = a.Y + (int64_t)j * a.ldY;
     for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
@@ -116,75 +208,7 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
     vo = block_sum_d(vo, sh);
     if (threadIdx.x == 0)
         a.obar[j] = (float)ob;
-
-    for (int li = 0; li < a.n_lib; ++li) {
-        const int64_t i = a.lib0 + li;
-        const uint8_t *lb = a.tables + (size_t)li * a.lay.lib_stride;
-        const float *Wt = reinterpret_cast<const float *>(lb + a.lay.off_w[E]);
-        const uint16_t *It = reinterpret_cast<const uint16_t *>(lb + a.lay.off_i[E]);
-        const size_t tq = (size_t)a.lay.Tq_pad;
-        float p[kBwMaxRows];
-#pragma unroll
-        for (int q = 0; q < kBwMaxRows; ++q) {
-            const int r = threadIdx.x + q * kBwThreads;
-            p[q] = 0.f;
-            if (r < Tq) {
-                float acc = 0.f;
-                for (int nn = 0; nn < k; ++nn)
-                    acc = fmaf(Wt[nn * tq + r], y[It[nn * tq + r]], acc);
-                p[q] = acc;
-            }
-        }
-        if (threadIdx.x == 0)
-            shK = p[0];  // row 0 (Tq >= 1)
-        __syncthreads();
-        const float K0 = shK;
-        float sdf = 0.f;
-#pragma unroll
-        for (int q = 0; q < kBwMaxRows; ++q)
-            if (threadIdx.x + q * kBwThreads < Tq)
-                sdf += p[q] - K0;
-        const double db = block_sum_f(sdf, sh) / n;
-        const double pb = (double)K0 + db;
-        const float dbf = (float)db, obf = (float)ob;
-        float vpf = 0.f, cf = 0.f;
-#pragma unroll
-        for (int q = 0; q < kBwMaxRows; ++q) {
-            const int r = threadIdx.x + q * kBwThreads;
-            if (r < Tq) {
-                const float dp = (p[q] - K0) - dbf;
-                vpf = fmaf(dp, dp, vpf);
-                cf = fmaf(dp, y[L + r + a.Tp] - obf, cf);
-            }
-        }
-        const double vp = block_sum_f(vpf, sh);
-        const double c = block_sum_f(cf, sh);
-        const double g = (double)a.grad_rho[(int64_t)j * a.ld_g + i];
-        double alpha = 0.0, beta = 0.0, gam = 0.0;
-        if (vp > 0.0 && vo > 0.0) {
-            const double sq = sqrt(vp * vo);
-            const double rho = c / sq;
-            alpha = g / sq;
-            beta = g * rho / vp;
-            gam = g * rho / vo;
-        }
-        if (threadIdx.x == 0)
-            a.stats[i * a.N + j] = make_float4((float)alpha, (float)beta, (float)pb, 0.f);
-        const float fa = (float)alpha, fb = (float)beta, fg = (float)gam, fpb = (float)pb, fob = (float)ob;
-#pragma unroll
-        for (int q = 0; q < kBwMaxRows; ++q) {
-            const int r = threadIdx.x + q * kBwThreads;
-            if (r < Tq) {
-                const float ov = y[L + r + a.Tp] - fob, pv = p[q] - fpb;
-                const float at = fa * ov - fb * pv;
-                const float bt = fa * pv - fg * ov;
-                for (int nn = 0; nn < k; ++nn)
-                    atomicAdd(&gy[It[nn * tq + r]], at * Wt[nn * tq + r]);
-                atomicAdd(&gy[L + r + a.Tp], bt);
-            }
-        }
-        __syncthreads();
-    }
+    bw_target_libs(a, y, gy, j, E, k, L, Tq, ob, vo, sh, ps);
     float *dst = a.grad_Y + (int64_t)j * a.ldY;
     for (int t = threadIdx.x; t < a.T; t += blockDim.x)
         dst[t] += gy[t];
