@@ -130,3 +130,23 @@ def test_long_series_limits_and_workspace_need_no_gpu(lib):
     # the batched form keeps its tiles in shared memory: about 3,100 steps at most
     long_set = (edm_dataset * 1)(edm_dataset(0x1000, 64, 5000, 5000, 0x1000, 0x1000, 64))
     assert lib.edm_ccm_rho_batched(long_set, 1, ctypes.byref(p), fake, 1 << 40, None) == 5
+
+
+def test_backward_workspace_holds_every_library_up_to_1gb(lib):
+    """The adjoint's table budget: the tables of all N libraries while they fit
+    in 1 GB (one block: the library pass then runs one CTA per library over
+    all of them), else 1 GB of tables; the rest (N^2 pair statistics, plans)
+    grows with N^2 and N."""
+    from paper_2011_11082_gb300 import edm_ccm_backward_workspace_bytes as ws
+
+    for T in (1500, 3000):
+        per_lib = ws(2, T) - ws(1, T)  # one library's tables (plus a few aligned bytes)
+        assert per_lib > 200 * T  # every E's table: sum_E (E+1) rows of (4 + 2) bytes, ~1.4 KB per step
+        # below the cap the tables grow by one library's bytes per library
+        n_fit = (1 << 30) // per_lib
+        assert abs((ws(n_fit, T) - ws(n_fit // 2, T)) - (n_fit - n_fit // 2) * per_lib) < 0.02 * ws(n_fit, T)
+        # above it the tables stay at 1 GB: only the N^2 statistics grow
+        big = 4 * n_fit
+        extra = ws(2 * big, T) - ws(big, T)
+        assert extra < 16 * ((2 * big) ** 2 - big ** 2) + 64 * big + (1 << 20)
+        assert ws(big, T) >= (1 << 30) + 16 * big * big
