@@ -263,8 +263,13 @@ int edm_ccm_rho_batched_reset(void);
  *   grad_rho  TARGET-MAJOR like rho: grad_rho[j*ld_g + i] = dL/d rho(i,j),
  *             ld_g >= N
  *   grad_Y    [N][ldY] float32, overwritten
- *   ws        at least edm_ccm_backward_workspace_bytes(N, T, params)
- * Requires T - Tp <= 3072.  The E grouping is planned on the device (no
+ *   ws        at least edm_ccm_backward_workspace_bytes(N, T, params):
+ *             16 bytes per (library, target) pair of statistics, plus the
+ *             kNN tables of every E for min(N, the libraries that fit in
+ *             1 GB) libraries at once (about 1.4 KB per library and time
+ *             step), processed in blocks of that many libraries
+ * Requires T - Tp <= 3072.  A pair with a zero-variance side (rho NaN in
+ * the forward map) contributes no gradient.  The E grouping is planned on the device (no
  * synchronisation); a target whose optE is outside 1..EDM_MAX_E (or leaves
  * fewer than E+1 candidates) contributes no gradient.
  * Summation order of the shared-memory accumulations varies between runs
