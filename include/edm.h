@@ -335,7 +335,9 @@ int edm_knn_counters(int64_t *reranks, int64_t *exhaustive, int reset);
  * target tiles in shared memory with bulk copies completed on an mbarrier,
  * and poll it a bounded number of times.  A wait that gives up makes its
  * CTA skip its work (its outputs are left unwritten) and counts here, so a
- * healthy run reads 0.  Synchronises the device.
+ * healthy run reads 0.  (The adjoint's library pass, which double-buffers
+ * target series the same way, loads a late series with plain loads instead
+ * and counts here too.)  Synchronises the device.
  */
 int edm_wait_timeouts(int64_t *count, int reset);
 

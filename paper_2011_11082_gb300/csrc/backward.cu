@@ -27,6 +27,7 @@
 // means, variances and coefficients are FP64.
 #include <algorithm>
 
+#include "bulk_copy.cuh"
 #include "edm_internal.cuh"
 #include "launchers.h"
 
@@ -217,14 +218,26 @@ __global__ void __launch_bounds__(kBwThreads) bw_target_kernel(BwArgs a)
 // Pass 2: one CTA per library in the block.  For each E, in chunks of
 // rows: the chunk's table entries (W and I) are staged in shared memory
 // once, then every target of that E adds its terms to H [k][rows of the
-// chunk] from shared memory only.
-__global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int buf_bytes)
+// chunk] from shared memory only.  With dbl (rows 16-byte aligned, T a
+// multiple of 4) the target series are double-buffered: while one target's
+// terms are added, a bulk copy brings the next target's series into the
+// other buffer.
+__global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int buf_bytes, int dbl)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long ybar[2];
     float *x = reinterpret_cast<float *>(smem);
     float *gx = x + a.T;
-    float *yb = gx + a.T;
-    unsigned char *buf = reinterpret_cast<unsigned char *>(yb + a.T);
+    float *const yb0 = gx + a.T, *const yb1 = gx + 2 * a.T;  // yb1 only with dbl
+    unsigned char *buf = reinterpret_cast<unsigned char *>(gx + (dbl ? 3 : 2) * a.T);
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&ybar[0]);
+    const uint32_t bar1 = (uint32_t)__cvta_generic_to_shared(&ybar[1]);
+    const uint32_t ybytes = (uint32_t)a.T * 4u;
+    uint32_t par0 = 0u, par1 = 0u;  // phase of each buffer's next completion
+    if (dbl && threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+    }
     const int li = blockIdx.x;
     const int64_t i = a.lib0 + li;
     const float *src = a.Y + i * a.ldY;
@@ -259,12 +272,42 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int bu
                 Is[nn * h_rows + rr] = It[nn * tq + r0 + rr];
             }
             __syncthreads();
+            if (dbl && threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(bar0, ybytes);
+                bulk_g2s((uint32_t)__cvta_generic_to_shared(yb0), a.Y + (int64_t)a.pi[j0] * a.ldY, ybytes, bar0);
+            }
             for (int pj = j0; pj < j1; ++pj) {
                 const int j = a.pi[pj];
                 const float *ys = a.Y + (int64_t)j * a.ldY;
-                for (int t = threadIdx.x; t < a.T; t += blockDim.x)
-                    yb[t] = ys[t];
-                __syncthreads();
+                const bool odd = dbl && ((pj - j0) & 1);
+                float *yb = odd ? yb1 : yb0;
+                if (dbl) {
+                    // the other buffer was last read before the barrier that
+                    // ended the previous target: refill it with the next one
+                    if (threadIdx.x == 0 && pj + 1 < j1) {
+                        fence_proxy_async_smem();
+                        mbar_expect_tx(odd ? bar0 : bar1, ybytes);
+                        bulk_g2s((uint32_t)__cvta_generic_to_shared(odd ? yb0 : yb1),
+                                 a.Y + (int64_t)a.pi[pj + 1] * a.ldY, ybytes, odd ? bar0 : bar1);
+                    }
+                    const bool got = mbar_wait(odd ? bar1 : bar0, odd ? par1 : par0);
+                    if (odd)
+                        par1 ^= 1u;
+                    else
+                        par0 ^= 1u;
+                    if (!__syncthreads_and(got)) {
+                        // a copy that did not arrive in time (counted): load
+                        // the row here (a late copy writes the same values)
+                        for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+                            yb[t] = ys[t];
+                        __syncthreads();
+                    }
+                } else {
+                    for (int t = threadIdx.x; t < a.T; t += blockDim.x)
+                        yb[t] = ys[t];
+                    __syncthreads();
+                }
                 const float4 st = a.stats[i * a.N + j];
                 const float ob = a.obar[j];
                 for (int rr = threadIdx.x; rr < rn; rr += blockDim.x) {
@@ -331,10 +374,13 @@ __global__ void __launch_bounds__(kBwThreads) bw_library_kernel(BwArgs a, int bu
 
 int bw_max_T() { return kBwMaxRows * kBwThreads; }
 
-// Library pass: x, gx and one target series (3T floats) and a buffer for a
-// chunk's H, W and I (10 bytes per row and neighbour), sized for about
-// 110 KB per CTA (two CTAs per SM) and at least 4 rows of the largest K.
-static size_t bw_lib_smem(int T, size_t buf_bytes) { return (size_t)3 * T * 4 + buf_bytes; }
+EDM_WAIT_TIMEOUT_READER(backward_wait_timeouts)
+
+// Library pass: x, gx and one or two target series (3T or 4T floats) and a
+// buffer for a chunk's H, W and I (10 bytes per row and neighbour), sized
+// for about 110 KB per CTA (two CTAs per SM) and at least 4 rows of the
+// largest K.
+static size_t bw_lib_smem(int T, int dbl, size_t buf_bytes) { return (size_t)(dbl ? 4 : 3) * T * 4 + buf_bytes; }
 
 cudaError_t launch_backward(const BwArgs &a, int kmax, cudaStream_t st)
 {
@@ -345,19 +391,24 @@ cudaError_t launch_backward(const BwArgs &a, int kmax, cudaStream_t st)
     bw_target_kernel<<<a.N, kBwThreads, s1, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    const size_t fixed = (size_t)3 * a.T * 4;
+    // double-buffered target series when every row is a 16-byte aligned bulk copy
+    const int dbl = (a.T % 4 == 0 && a.ldY % 4 == 0 && (reinterpret_cast<uintptr_t>(a.Y) & 15) == 0 &&
+                     (size_t)a.T * 4 < (1u << 20))
+                        ? 1
+                        : 0;
+    const size_t fixed = (size_t)(dbl ? 4 : 3) * a.T * 4;
     const size_t target = 110 * 1024;
     const size_t floor_bytes = (size_t)10 * kmax * 8;
     size_t buf = target > fixed + floor_bytes ? target - fixed : floor_bytes;
     buf = std::min(buf, (size_t)10 * kmax * (size_t)(a.T + 3));
     buf &= ~(size_t)15;
-    const size_t s2 = bw_lib_smem(a.T, buf);
+    const size_t s2 = bw_lib_smem(a.T, dbl, buf);
     if (s2 > 227 * 1024)
         return cudaErrorInvalidValue;
     if ((e = cudaFuncSetAttribute(bw_library_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2)) !=
         cudaSuccess)
         return e;
-    bw_library_kernel<<<a.n_lib, kBwThreads, s2, st>>>(a, (int)buf);
+    bw_library_kernel<<<a.n_lib, kBwThreads, s2, st>>>(a, (int)buf, dbl);
     return cudaGetLastError();
 }
 

@@ -314,7 +314,7 @@ int edm_wait_timeouts(int64_t *count, int reset)
     cudaError_t (*readers[])(unsigned long long *, bool) = {
         edm::knn_wait_timeouts, edm::knn_thread_wait_timeouts, edm::lookup_multi128_wait_timeouts,
         edm::lookup_multi128_lag_wait_timeouts, edm::lookup_multi64_wait_timeouts,
-        edm::lookup_multi64_lag_wait_timeouts};
+        edm::lookup_multi64_lag_wait_timeouts, edm::backward_wait_timeouts};
     unsigned long long tot = 0ull;
     for (auto rd : readers) {
         unsigned long long c = 0ull;

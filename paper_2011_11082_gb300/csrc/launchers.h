@@ -67,6 +67,7 @@ cudaError_t lookup_multi128_wait_timeouts(unsigned long long *count, bool reset)
 cudaError_t lookup_multi128_lag_wait_timeouts(unsigned long long *count, bool reset);
 cudaError_t lookup_multi64_wait_timeouts(unsigned long long *count, bool reset);
 cudaError_t lookup_multi64_lag_wait_timeouts(unsigned long long *count, bool reset);
+cudaError_t backward_wait_timeouts(unsigned long long *count, bool reset);
 
 // Public table format: idx int32 [n_lib][Tq][E+1] (unshifted), w float [n_lib][Tq][E+1].
 cudaError_t launch_knn_public(const float *Y, int64_t ldY, int n_lib, int T, int E, int tau, int Tp, int excl,
