@@ -116,8 +116,8 @@ def edm_knn_counters(reset: bool = True) -> tuple[int, int]:
 
 
 def edm_wait_timeouts(reset: bool = True) -> int:
-    """Bounded bulk-copy waits of the kNN and lookup kernels that gave up
-    since the last reset (0 in a healthy run; synchronises)."""
+    """Bounded bulk-copy waits of the kNN, lookup and adjoint kernels that
+    gave up since the last reset (0 in a healthy run; synchronises)."""
     lib = _abi.load()
     a = ctypes.c_int64()
     _abi.check(lib.edm_wait_timeouts(ctypes.byref(a), 1 if reset else 0), "edm_wait_timeouts")
